@@ -1,0 +1,222 @@
+/*
+ * helm.h -- C-ABI of libhelm: multi-source frequency-domain Helmholtz solves
+ * on one GB300 (sm_103a) with a shifted-Laplacian multigrid preconditioned
+ * block flexible GMRES.
+ *
+ * Problem (Treister & Haber, Sec. 2.1 Eq. helm and Sec. 2.4 Eq.
+ * LinearSystem), in this library's sign convention:
+ *
+ *     A u := -Lap_h u - omega^2 m (1 - i gamma) u = q,
+ *
+ * with the second-order 5-point (2D) / 7-point (3D) Laplacian on the nodes
+ * of a regular grid, Dirichlet zero beyond the node grid, squared slowness m
+ * and a dimensionless attenuation gamma that carries the absorbing layer.
+ * (The paper writes Lap_h u + omega^2 (1 - i gamma_p/omega) m u = q; so
+ * gamma = gamma_p/omega and u = -u_paper.)
+ *
+ * Preconditioner (Sec. 4): one multigrid V-cycle for the shifted operator
+ * M = A with gamma -> gamma + shift, Galerkin coarse operators
+ * M_{l+1} = P^T M_l P with bi/trilinear P, damped Jacobi relaxation and a
+ * dense LU (stored as the inverse) on the coarsest grid (Sec. 4, Alg.
+ * "Two-grid cycle"; Sec. 5.3 settings: 2 pre + 2 post sweeps, weight 0.8).
+ * Krylov method: block FGMRES(m) (Sec. 5.3), run on groups of `block`
+ * right-hand sides that advance in lock step and share every kernel launch.
+ *
+ * Layouts
+ *   Node index: x1 fastest, then x2, then x3; n[k] cells give n[k]+1 nodes.
+ *   ABI block (helm_solve, helm_adjoint): complex128 (interleaved re, im),
+ *     N x s column-major, i.e. column j (one right-hand side) is the N
+ *     contiguous complex values Q[j*N .. j*N+N-1].
+ *   Internal block (component entry points below): node-major with the
+ *     right-hand sides innermost, x[node*s + j]; complex128 or complex64 as
+ *     the `prec` argument says.
+ *
+ * Ownership and ordering
+ *   The caller owns every buffer it passes; the context owns its hierarchy
+ *   and workspace (device memory allocated with cudaMalloc at set-up and,
+ *   when a larger s is first seen, at the first solve with that s).  All
+ *   device work is enqueued on the stream given to helm_setup; every call
+ *   returns after that stream has been synchronised.  Pointers marked
+ *   "device" must be device (or managed) memory of the current device.
+ *
+ * Errors
+ *   Every call returns a helm_status; no exception crosses the ABI.  On any
+ *   status other than HELM_OK, helm_last_error() describes it.  A solve that
+ *   stops early (HELM_NOT_CONVERGED, HELM_ERR_NONFINITE) still writes the
+ *   best iterate to U and fills `info`.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx helm_ctx;
+
+typedef enum {
+    HELM_OK = 0,
+    HELM_ERR_ARG = 1,          /* bad argument (sizes, pointers, levels)      */
+    HELM_ERR_NOMEM = 2,        /* device or host allocation failed            */
+    HELM_ERR_CUDA = 3,         /* a CUDA runtime call failed                  */
+    HELM_NOT_CONVERGED = 4,    /* iteration cap reached; U = best iterate     */
+    HELM_ERR_NONFINITE = 5,    /* NaN/Inf met in an FP64 residual norm        */
+    HELM_ERR_BREAKDOWN = 6     /* singular coarsest operator or Krylov block  */
+} helm_status;
+
+typedef enum {
+    HELM_PLAIN_C128 = 0,        /* every step in complex128 (FP64)             */
+    HELM_MIXED_C64 = 1,         /* V-cycle in complex64 with FP32 accumulation;
+                                   A*Z, residuals, orthogonalisation, QR and
+                                   least squares in FP64                       */
+    HELM_MIXED_C64_LEARNED = 2  /* HELM_MIXED_C64 plus the learned stage       */
+} helm_prec;
+
+typedef struct {
+    int dim;                 /* 2 or 3                                          */
+    int n[3];                /* cells per axis (x1, x2, x3); nodes = n[k]+1;
+                                every n[k] divisible by 2^(levels-1)            */
+    double h;                /* grid spacing (same on every axis)               */
+    double omega;            /* angular frequency                               */
+    double shift;            /* beta added to gamma in the preconditioner (0.5) */
+    int levels;              /* multigrid levels, >= 1 (1 = dense solve only)   */
+    int pre, post;           /* Jacobi sweeps before / after the coarse
+                                correction (2, 2)                               */
+    double jacobi_w;         /* Jacobi damping (0.8)                            */
+    int restart;             /* FGMRES(m): block steps per restart cycle (10)   */
+    int block;               /* right-hand sides per Krylov block (>= 1)        */
+    int max_restarts;        /* restart cycles before HELM_NOT_CONVERGED        */
+    helm_prec prec;          /* precision policy                                */
+    const void* learned_weights; /* device BF16 weights of the learned stage
+                                    (layout in helm_learned.h); NULL = none     */
+} helm_params;
+
+typedef struct {
+    int* iters;     /* per column: preconditioner applications (the paper's
+                       #Cyc, Sec. 5.3 table), caller-owned host array of s   */
+    double* relres; /* per column: true ||q - A u|| / ||q|| in FP64 (0 for a
+                       zero column), caller-owned host array of s             */
+    int* status;    /* per column: helm_status, caller-owned host array of s  */
+} helm_info;
+
+/* Fill p with the defaults of Sec. 5.3 (levels 3, V(2,2), weight 0.8,
+   restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128. */
+void helm_default_params(helm_params* p);
+
+/* Set up the hierarchy for one (m, gamma, omega) (Sec. 4: set-up once, reused
+   by every right-hand side and by the adjoint solve).
+   m, gamma_tilde: device float64 arrays of N = prod(n[k]+1) node values,
+   copied; cuda_stream: a cudaStream_t (NULL = legacy default stream).
+   Builds A's and M's fine-level coefficients, the Galerkin coefficients of
+   every coarse level, the Jacobi inverse diagonals and the FP64 inverse of
+   the coarsest operator (Gauss-Jordan with partial pivoting).
+   Returns HELM_ERR_ARG for bad sizes, HELM_ERR_BREAKDOWN when the coarsest
+   operator is singular. */
+helm_status helm_setup(const double* m, const double* gamma_tilde,
+                       const helm_params* p, void* cuda_stream, helm_ctx** out);
+
+/* Solve A U = Q for s right-hand sides to per-column relative residual tol
+   (FP64, true residual), X_0 = 0 (Sec. 5.3: block FGMRES preconditioned by
+   the shifted-Laplacian cycle).  Q, U: device complex128, ABI layout, N x s.
+   A zero column gives a zero solution with relres 0.  info may be NULL. */
+helm_status helm_solve(helm_ctx* ctx, const void* Q, int s, double tol,
+                       void* U, helm_info* info);
+
+/* Solve A^H L = B (the adjoint solve of the sensitivity, Sec. 2.4 Eq.
+   fwisens; Sec. 4 last paragraph: same hierarchy).  A is complex symmetric,
+   so L = conj(A^{-1} conj(B)).  Same layout and semantics as helm_solve. */
+helm_status helm_adjoint(helm_ctx* ctx, const void* B, int s, double tol,
+                         void* L, helm_info* info);
+
+/* helm_solve with HOST complex128 buffers (ABI layout): copies Q to the
+   device, solves, copies U back, all on the context's stream.  Pinned host
+   memory makes the copies asynchronous DMA; pageable memory works too. */
+helm_status helm_solve_host(helm_ctx* ctx, const void* Q_host, int s,
+                            double tol, void* U_host, helm_info* info);
+
+/* Solve several independent problems (contexts, possibly different grids,
+   frequencies and precisions): problem k solves ctxs[k] with Q[k] (s[k]
+   columns) into U[k], infos[k] (may be NULL).  Problems are ordered by the
+   autotuned cost model and their block steps are interleaved on the
+   contexts' streams.  Returns the first non-OK status (all are attempted). */
+helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* Q,
+                             const int* s, int nprob, double tol,
+                             void* const* U, helm_info* infos);
+
+void helm_destroy(helm_ctx* ctx);
+
+/* Message of the last error of ctx (or of this thread when ctx is NULL). */
+const char* helm_last_error(const helm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Component entry points (internal layout, device pointers).  They expose
+ * the hot-path steps one by one so that each can be checked on its own.
+ * `prec`: 0 = complex128 vectors and FP64 arithmetic, 1 = complex64 vectors
+ * and FP32 arithmetic (coefficients rounded from the FP64 set-up).
+ * Level 0 is the fine grid; level levels-1 the coarsest.
+ * ------------------------------------------------------------------- */
+
+/* Nodes per axis (nodes[3], unused axes 1) and node count of a level. */
+helm_status helm_level_shape(const helm_ctx* ctx, int level, int* nodes,
+                             long long* count);
+
+/* y = Op x for s columns.  op = 0: A (level 0 only), op = 1: M_level
+   (fine: 5/7-point stencil, Sec. 2.4; coarse: Galerkin P^T M P, Sec. 4). */
+helm_status helm_apply(helm_ctx* ctx, int level, int op, int prec,
+                       const void* x, void* y, int s);
+
+/* Damped Jacobi on M_level (Sec. 5.3): `sweeps` times
+   u <- u + w D^{-1} (f - M u), starting from u_in (NULL = zero). */
+helm_status helm_smooth(helm_ctx* ctx, int level, int prec, const void* u_in,
+                        const void* f, void* u_out, int s, int sweeps);
+
+/* rc = P^T (f - M_level u) on level+1 (Alg. "Two-grid cycle" step 2). */
+helm_status helm_restrict_residual(helm_ctx* ctx, int level, int prec,
+                                   const void* u, const void* f, void* rc,
+                                   int s);
+
+/* u <- u + P ec (Alg. "Two-grid cycle" step 4), ec on level+1. */
+helm_status helm_prolong_add(helm_ctx* ctx, int level, int prec,
+                             const void* ec, void* u, int s);
+
+/* u = M_L^{-1} f on the coarsest level (dense inverse times the block). */
+helm_status helm_coarse_solve(helm_ctx* ctx, int prec, const void* f, void* u,
+                              int s);
+
+/* z = V-cycle(f) for M (zero initial guess).  f: complex128; z: complex128
+   (prec 0) or complex64 (prec 1). */
+helm_status helm_vcycle(helm_ctx* ctx, int prec, const void* f, void* z, int s);
+
+/* Copy the FP64 stencil of M_level to host: count x K complex128 values,
+   K = 9 (2D) or 27 (3D), offset o = sum_k (d_k+1) 3^k for d_k in {-1,0,1}
+   along axis k (x1 first); zero where the neighbour is outside the grid.
+   Level 0 is returned in the same K-point form. */
+helm_status helm_get_operator(const helm_ctx* ctx, int level, void* coef_host);
+
+/* Number of kernels libhelm launched on this context since set-up. */
+long long helm_kernel_launches(const helm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Per-kernel profiler (the per-RHS timing of Sec. 5.3's table, broken down
+ * by kernel).  When enabled, every launch on the context is bracketed by a
+ * CUDA event pair on the context's stream and tagged with its algorithmic
+ * bytes and flops (each vector element read or written once, coefficients
+ * once per node).  Enabling resets the totals; disabling frees the events.
+ * ------------------------------------------------------------------- */
+helm_status helm_profile_enable(helm_ctx* ctx, int enable);
+/* Number of kernel classes and the name of class kid (static strings). */
+int helm_profile_kernel_count(void);
+const char* helm_profile_kernel_name(int kid);
+/* Totals of class kid since enabling: summed event time (ms), launches,
+   algorithmic bytes and flops.  Synchronises the context's stream. */
+helm_status helm_profile_read(helm_ctx* ctx, int kid, double* time_ms, long long* launches,
+                              double* bytes, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HELM_H */

@@ -1,0 +1,171 @@
+// Device-side helpers shared by the libhelm kernels: complex arithmetic on
+// interleaved (re, im) pairs, the stencil operators of every level, and the
+// launch context (stream, launch counter, profiler) of every launcher.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace helm {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cplx {
+    T re, im;
+};
+
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> mk(T r, T i) { cplx<T> z; z.re = r; z.im = i; return z; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator*(T a, cplx<T> b) { return mk(a * b.re, a * b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> conj(cplx<T> a) { return mk(a.re, -a.im); }
+// a += b * c
+template <typename T>
+__host__ __device__ __forceinline__ void fma_acc(cplx<T>& a, cplx<T> b, cplx<T> c) {
+    a.re = fma(b.re, c.re, a.re); a.re = fma(-b.im, c.im, a.re);
+    a.im = fma(b.re, c.im, a.im); a.im = fma(b.im, c.re, a.im);
+}
+// a += conj(b) * c
+template <typename T>
+__host__ __device__ __forceinline__ void fma_conj_acc(cplx<T>& a, cplx<T> b, cplx<T> c) {
+    a.re = fma(b.re, c.re, a.re); a.re = fma(b.im, c.im, a.re);
+    a.im = fma(b.re, c.im, a.im); a.im = fma(-b.im, c.re, a.im);
+}
+
+template <typename To, typename From>
+__host__ __device__ __forceinline__ cplx<To> cvt(cplx<From> a) { return mk<To>((To)a.re, (To)a.im); }
+
+template <typename T>
+__device__ __forceinline__ cplx<T> ldg(const cplx<T>* p) {
+    cplx<T> z;
+    if (sizeof(T) == 8) {
+        double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        z.re = (T)v.x; z.im = (T)v.y;
+    } else {
+        float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        z.re = (T)v.x; z.im = (T)v.y;
+    }
+    return z;
+}
+
+// Grid of nodes; x1 fastest.  n[2] = 1 in 2D.
+struct Grid {
+    int dim;
+    int n1, n2, n3;
+    long long N;
+    __host__ __device__ __forceinline__ void coords(long long node, int& x, int& y, int& z) const {
+        x = (int)(node % n1);
+        long long t = node / n1;
+        y = (int)(t % n2);
+        z = (int)(t / n2);
+    }
+    __host__ __device__ __forceinline__ long long index(int x, int y, int z) const {
+        return ((long long)z * n2 + y) * n1 + x;
+    }
+};
+
+// Fine-level operator: y = (1/h^2) (2d u_i - sum_{axis nbrs} u_j) - c_i u_i
+// (Sec. 2.4: second-order finite differences), c = omega^2 m (1 - i gamma').
+template <typename T>
+struct FineOp {
+    Grid g;
+    T inv_h2;
+    const cplx<T>* c;     // mass coefficient per node
+    const cplx<T>* dinv;  // 1 / (2d/h^2 - c_i) per node (Jacobi); may be null
+
+    template <typename U>
+    __device__ __forceinline__ cplx<T> apply(const cplx<U>* u, long long node, int x, int y, int z,
+                                             int s, int r) const {
+        const cplx<U>* p = u + node * s + r;
+        cplx<T> ui = cvt<T>(ldg(p));
+        cplx<T> sum = mk<T>(0, 0);
+        if (x > 0) sum = sum + cvt<T>(ldg(p - s));
+        if (x < g.n1 - 1) sum = sum + cvt<T>(ldg(p + s));
+        long long sy = (long long)g.n1 * s;
+        if (y > 0) sum = sum + cvt<T>(ldg(p - sy));
+        if (y < g.n2 - 1) sum = sum + cvt<T>(ldg(p + sy));
+        if (g.dim == 3) {
+            long long sz = (long long)g.n1 * g.n2 * s;
+            if (z > 0) sum = sum + cvt<T>(ldg(p - sz));
+            if (z < g.n3 - 1) sum = sum + cvt<T>(ldg(p + sz));
+        }
+        T dd = (T)(2 * g.dim);
+        cplx<T> ci = ldg(c + node);
+        cplx<T> y_ = inv_h2 * mk<T>(dd * ui.re - sum.re, dd * ui.im - sum.im);
+        return y_ - ci * ui;
+    }
+    __device__ __forceinline__ cplx<T> diag_inv(long long node) const { return ldg(dinv + node); }
+};
+
+// Galerkin coarse operator: 9-point (2D) or 27-point (3D) stencil with
+// per-node complex coefficients coef[node*K + o], o = (dx+1) + 3(dy+1) [+ 9(dz+1)].
+template <typename T>
+struct GalOp {
+    Grid g;
+    const cplx<T>* coef;
+    const cplx<T>* dinv;
+
+    template <typename U>
+    __device__ __forceinline__ cplx<T> apply(const cplx<U>* u, long long node, int x, int y, int z,
+                                             int s, int r) const {
+        const int K = g.dim == 3 ? 27 : 9;
+        const cplx<T>* cf = coef + node * K;
+        cplx<T> acc = mk<T>(0, 0);
+        const int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
+        for (int dz = z0; dz <= z1; ++dz) {
+            int zz = z + dz;
+            if (zz < 0 || zz >= g.n3) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= g.n2) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= g.n1) continue;
+                    int o = (dx + 1) + 3 * (dy + 1) + (g.dim == 3 ? 9 * (dz + 1) : 0);
+                    cplx<T> cc = ldg(cf + o);
+                    cplx<T> uv = cvt<T>(ldg(u + g.index(xx, yy, zz) * s + r));
+                    fma_acc(acc, cc, uv);
+                }
+            }
+        }
+        return acc;
+    }
+    __device__ __forceinline__ cplx<T> diag_inv(long long node) const { return ldg(dinv + node); }
+};
+
+// Kernel classes seen by the profiler (helm_profile_* in helm.h).
+enum KernelId {
+    KID_APPLY_FINE = 0, KID_APPLY_COARSE, KID_RESIDUAL, KID_JACOBI_FINE, KID_JACOBI_COARSE,
+    KID_RESTRICT_FINE, KID_RESTRICT_COARSE, KID_PROLONG, KID_DENSE, KID_GRAM, KID_GRAM_REDUCE,
+    KID_COMBINE, KID_LAYOUT, KID_RANDOM, KID_SETUP, KID_COUNT
+};
+
+struct Profiler;  // host side, defined in solver.cu
+void prof_begin(Profiler* p, cudaStream_t st, int kid, double bytes, double flops);
+void prof_end(Profiler* p, cudaStream_t st);
+
+struct Launch {
+    cudaStream_t st;
+    long long* counter;  // incremented once per kernel launch
+    Profiler* prof;      // null unless profiling is on
+    // pre(): before a launch, with its algorithmic bytes and flops; post(): after it
+    void pre(int kid, double bytes, double flops) const {
+        if (prof) prof_begin(prof, st, kid, bytes, flops);
+    }
+    void post() const {
+        if (counter) ++*counter;
+        if (prof) prof_end(prof, st);
+    }
+};
+
+}  // namespace helm

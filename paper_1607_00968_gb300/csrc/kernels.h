@@ -1,0 +1,99 @@
+// Host-side launchers of the libhelm kernels (instantiated in mg.cu and
+// krylov.cu, called by the solver driver in solver.cu).
+#pragma once
+#include "common.cuh"
+
+namespace helm {
+
+// ---------------- multigrid (mg.cu) ----------------
+
+// y = Op x  (T: arithmetic precision; U: input element; V: output element)
+template <typename T, typename U, typename V, typename Op>
+void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, int s);
+
+// r = b - Op x
+template <typename T, typename Op>
+void launch_residual(const Launch& L, const Op& op, const cplx<T>* x, const cplx<T>* b,
+                     cplx<T>* r, int s);
+
+// u_out = u_in + w D^{-1} (f - Op u_in); u_in == nullptr means u_in = 0.
+template <typename T, typename FT, typename Op>
+void launch_jacobi(const Launch& L, const Op& op, const cplx<T>* u_in, const cplx<FT>* f,
+                   cplx<T>* u_out, int s, T w);
+
+// rc = P^T (f - Op u) on the coarse grid gc; u == nullptr means u = 0.
+template <typename T, typename FT, typename Op>
+void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const cplx<T>* u,
+                           const cplx<FT>* f, cplx<T>* rc, int s);
+
+// u += P ec
+template <typename T>
+void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const cplx<T>* ec,
+                        cplx<T>* u, int s);
+
+// u = Minv f  (Minv: n x n row-major; f, u: n x s node-major)
+template <typename T>
+void launch_dense_apply(const Launch& L, const cplx<T>* Minv, int n, const cplx<T>* f,
+                        cplx<T>* u, int s);
+
+// ---------------- set-up (mg.cu) ----------------
+
+// c_A = omega^2 m (1 - i gamma), c_M = omega^2 m (1 - i (gamma + shift)),
+// dinv_M = 1 / (2d/h^2 - c_M); also the K-point FP64 stencil of M (coef_M).
+void launch_fine_setup(const Launch& L, const Grid& g, const double* m, const double* gamma,
+                       double omega, double shift, double inv_h2, c128* cA, c128* cM,
+                       c128* dinvM, c128* coefM);
+
+// coarse K-point stencil = P^T (fine K-point stencil) P
+void launch_galerkin(const Launch& L, const Grid& gf, const Grid& gc, const c128* coef_f,
+                     c128* coef_c);
+
+// dinv[i] = 1 / coef[i*K + centre]
+void launch_diag_inv(const Launch& L, const Grid& g, const c128* coef, c128* dinv);
+
+// dense n x n matrix (row-major) of a K-point stencil
+void launch_stencil_to_dense(const Launch& L, const Grid& g, const c128* coef, c128* dense);
+
+// In-place Gauss-Jordan inversion with partial pivoting of the n x n matrix
+// held in the left half of aug (n x 2n, right half set to I here).  status
+// (device int) is set to 1 if a zero pivot is met.
+void launch_gauss_jordan(const Launch& L, c128* aug, int n, c128* factor, int* piv,
+                         c128* pivval, int* status);
+
+// out (n x n) = right half of aug; out32 = its complex64 rounding (may be null)
+void launch_extract_inverse(const Launch& L, const c128* aug, int n, c128* out, c64* out32);
+
+void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count);
+
+// ---------------- Krylov / layout (krylov.cu) ----------------
+
+// internal[node*s + j] = (conj?) abi[j*N + node]
+void launch_to_internal(const Launch& L, const c128* abi, c128* internal, long long N, int s,
+                        bool conjugate);
+void launch_from_internal(const Launch& L, const c128* internal, c128* abi, long long N, int s,
+                          bool conjugate);
+
+// Block Gram per group:  out[i][g][a][b] = sum_node conj(X_i[node][g*sb+a]) Y[node][g*sb+b]
+// for i < nb (X_i = X + i*xstride).  partial: scratch of gram_partial_elems().
+long long gram_partial_elems(long long N, int nb, int s, int sb);
+void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
+                 long long N, int s, int sb, c128* partial, c128* out);
+
+// out[node][g*sb+b] = beta*out + sign * sum_{i<nb} sum_a X_i[node][g*sb+a] C[i][g][a][b]
+template <typename TX>
+void launch_combine(const Launch& L, c128* out, double beta, double sign, const cplx<TX>* X,
+                    int nb, long long xstride, const c128* C, long long N, int s, int sb);
+
+// per-column squared 2-norms of X (N x s node-major): out[j] (FP64)
+long long colnorm_partial_elems(long long N, int s);
+void launch_colnorm2(const Launch& L, const c128* X, long long N, int s, double* partial,
+                     double* out);
+
+// X[node][j] = random complex (counter-based hash of (seed, node, j)) for
+// columns with mask[j] != 0; other columns untouched.
+void launch_fill_random(const Launch& L, c128* X, long long N, int s, const int* mask,
+                        unsigned long long seed);
+
+void launch_zero(const Launch& L, void* p, size_t bytes);
+
+}  // namespace helm

@@ -1,0 +1,585 @@
+// Multigrid kernels of the shifted-Laplacian preconditioner (Sec. 4, Alg.
+// "Two-grid cycle"): stencil apply, damped Jacobi, fused residual +
+// restriction, prolongation + correction, coarsest dense solve; and the
+// set-up kernels (fine coefficients, Galerkin P^T M P, Gauss-Jordan inverse).
+//
+// Vectors are node-major with the s right-hand sides innermost
+// (x[node*s + j]); one thread owns one (node, column) element, so a warp
+// reads contiguous memory and the stencil neighbours of one node are s
+// elements apart (x1) or one grid row / plane apart (x2, x3).
+#include "kernels.h"
+
+namespace helm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long total) {
+    long long b = (total + kThreads - 1) / kThreads;
+    if (b < 1) b = 1;
+    if (b > 0x7fffffffLL) b = 0x7fffffffLL;
+    return (int)b;
+}
+
+template <typename T, typename U, typename V, typename Op>
+__global__ void __launch_bounds__(kThreads) k_apply(Op op, const cplx<U>* __restrict__ x,
+                                                     cplx<V>* __restrict__ y, int s,
+                                                     long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long node = e / s;
+        int r = (int)(e - node * s);
+        int a, b, c;
+        op.g.coords(node, a, b, c);
+        cplx<T> v = op.apply(x, node, a, b, c, s, r);
+        y[e] = cvt<V>(v);
+    }
+}
+
+template <typename T, typename Op>
+__global__ void __launch_bounds__(kThreads) k_residual(Op op, const cplx<T>* __restrict__ x,
+                                                        const cplx<T>* __restrict__ bv,
+                                                        cplx<T>* __restrict__ r_, int s,
+                                                        long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long node = e / s;
+        int r = (int)(e - node * s);
+        int a, b, c;
+        op.g.coords(node, a, b, c);
+        r_[e] = ldg(bv + e) - op.apply(x, node, a, b, c, s, r);
+    }
+}
+
+template <typename T, typename FT, typename Op>
+__global__ void __launch_bounds__(kThreads) k_jacobi(Op op, const cplx<T>* __restrict__ uin,
+                                                      const cplx<FT>* __restrict__ f,
+                                                      cplx<T>* __restrict__ uout, int s, T w,
+                                                      long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long node = e / s;
+        int r = (int)(e - node * s);
+        cplx<T> fi = cvt<T>(ldg(f + e));
+        cplx<T> d = op.diag_inv(node);
+        if (uin == nullptr) {
+            uout[e] = w * (d * fi);
+        } else {
+            int a, b, c;
+            op.g.coords(node, a, b, c);
+            cplx<T> Au = op.apply(uin, node, a, b, c, s, r);
+            cplx<T> ui = ldg(uin + e);
+            uout[e] = ui + w * (d * (fi - Au));
+        }
+    }
+}
+
+// rc[J] = sum over fine nodes i = 2J + delta of prod_k w(delta_k) (f - Op u)_i,
+// w(0) = 1, w(+-1) = 1/2 (full weighting with R = P^T, Sec. 4).
+template <typename T, typename FT, typename Op>
+__global__ void __launch_bounds__(kThreads) k_resid_restrict(Op op, Grid gc,
+                                                              const cplx<T>* __restrict__ u,
+                                                              const cplx<FT>* __restrict__ f,
+                                                              cplx<T>* __restrict__ rc, int s,
+                                                              long long total) {
+    const Grid& gf = op.g;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long J = e / s;
+        int r = (int)(e - J * s);
+        int jx, jy, jz;
+        gc.coords(J, jx, jy, jz);
+        cplx<T> acc = mk<T>(0, 0);
+        const int z0 = gf.dim == 3 ? -1 : 0, z1 = gf.dim == 3 ? 1 : 0;
+        for (int dz = z0; dz <= z1; ++dz) {
+            int fz = gf.dim == 3 ? 2 * jz + dz : 0;
+            if (fz < 0 || fz >= gf.n3) continue;
+            T wz = dz == 0 ? T(1) : T(0.5);
+            for (int dy = -1; dy <= 1; ++dy) {
+                int fy = 2 * jy + dy;
+                if (fy < 0 || fy >= gf.n2) continue;
+                T wy = dy == 0 ? wz : T(0.5) * wz;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int fx = 2 * jx + dx;
+                    if (fx < 0 || fx >= gf.n1) continue;
+                    T wgt = dx == 0 ? wy : T(0.5) * wy;
+                    long long i = gf.index(fx, fy, fz);
+                    cplx<T> ri = cvt<T>(ldg(f + i * s + r));
+                    if (u != nullptr) ri = ri - op.apply(u, i, fx, fy, fz, s, r);
+                    acc = acc + wgt * ri;
+                }
+            }
+        }
+        rc[e] = acc;
+    }
+}
+
+// u_i += sum_J P_iJ ec_J: per axis an even fine index takes coarse i/2 with
+// weight 1, an odd one the two neighbours with weight 1/2 (bilinear, Sec. 4).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_prolong_add(Grid gf, Grid gc,
+                                                           const cplx<T>* __restrict__ ec,
+                                                           cplx<T>* __restrict__ u, int s,
+                                                           long long total) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        long long node = e / s;
+        int r = (int)(e - node * s);
+        int x, y, z;
+        gf.coords(node, x, y, z);
+        int xs[2], ys[2], zs[2];
+        int nx = (x & 1) ? 2 : 1, ny = (y & 1) ? 2 : 1, nz = (gf.dim == 3 && (z & 1)) ? 2 : 1;
+        xs[0] = x >> 1; xs[1] = (x >> 1) + 1;
+        ys[0] = y >> 1; ys[1] = (y >> 1) + 1;
+        zs[0] = z >> 1; zs[1] = (z >> 1) + 1;
+        T w = T(1);
+        if (nx == 2) w *= T(0.5);
+        if (ny == 2) w *= T(0.5);
+        if (nz == 2) w *= T(0.5);
+        cplx<T> acc = mk<T>(0, 0);
+        for (int c = 0; c < nz; ++c)
+            for (int b = 0; b < ny; ++b)
+                for (int a = 0; a < nx; ++a)
+                    acc = acc + ldg(ec + gc.index(xs[a], ys[b], zs[c]) * s + r);
+        u[e] = ldg(u + e) + w * acc;
+    }
+}
+
+// u = Minv f: tiled complex GEMM (n x n) * (n x s), 32 x 32 output tile per
+// block, 16-deep k tiles staged in shared memory, 4 outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_apply(const cplx<T>* __restrict__ A, int n,
+                                                      const cplx<T>* __restrict__ B,
+                                                      cplx<T>* __restrict__ C, int s) {
+    constexpr int TM = 32, TN = 32, TK = 16;
+    __shared__ cplx<T> As[TM][TK + 1];
+    __shared__ cplx<T> Bs[TK][TN];
+    const int tid = threadIdx.x;
+    const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    const int tc = tid % TN;       // output column within the tile
+    const int tr = tid / TN;       // 0..7: rows tr, tr+8, tr+16, tr+24
+    cplx<T> acc[4];
+    for (int q = 0; q < 4; ++q) acc[q] = mk<T>(0, 0);
+    for (int k0 = 0; k0 < n; k0 += TK) {
+        for (int idx = tid; idx < TM * TK; idx += 256) {
+            int rr = idx / TK, kk = idx % TK;
+            int gr = row0 + rr, gk = k0 + kk;
+            As[rr][kk] = (gr < n && gk < n) ? ldg(A + (long long)gr * n + gk) : mk<T>(0, 0);
+        }
+        for (int idx = tid; idx < TK * TN; idx += 256) {
+            int kk = idx / TN, cc = idx % TN;
+            int gk = k0 + kk, gc = col0 + cc;
+            Bs[kk][cc] = (gk < n && gc < s) ? ldg(B + (long long)gk * s + gc) : mk<T>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            cplx<T> bv = Bs[kk][tc];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fma_acc(acc[q], As[tr + 8 * q][kk], bv);
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        int gr = row0 + tr + 8 * q, gc = col0 + tc;
+        if (gr < n && gc < s) C[(long long)gr * s + gc] = acc[q];
+    }
+}
+
+// ---------------- set-up ----------------
+
+__global__ void k_fine_setup(Grid g, const double* __restrict__ m, const double* __restrict__ gam,
+                             double omega, double shift, double inv_h2, c128* cA, c128* cM,
+                             c128* dinvM, c128* coefM) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    double w2m = omega * omega * m[i];
+    c128 a = mk(w2m, -w2m * gam[i]);
+    c128 b = mk(w2m, -w2m * (gam[i] + shift));
+    cA[i] = a;
+    cM[i] = b;
+    c128 d = mk(2.0 * g.dim * inv_h2 - b.re, -b.im);
+    double den = d.re * d.re + d.im * d.im;
+    dinvM[i] = mk(d.re / den, -d.im / den);
+    const int K = g.dim == 3 ? 27 : 9;
+    int x, y, z;
+    g.coords(i, x, y, z);
+    c128* cf = coefM + i * K;
+    for (int o = 0; o < K; ++o) cf[o] = mk(0.0, 0.0);
+    int ctr = g.dim == 3 ? 13 : 4;
+    cf[ctr] = d;
+    if (x > 0) cf[ctr - 1] = mk(-inv_h2, 0.0);
+    if (x < g.n1 - 1) cf[ctr + 1] = mk(-inv_h2, 0.0);
+    if (y > 0) cf[ctr - 3] = mk(-inv_h2, 0.0);
+    if (y < g.n2 - 1) cf[ctr + 3] = mk(-inv_h2, 0.0);
+    if (g.dim == 3) {
+        if (z > 0) cf[ctr - 9] = mk(-inv_h2, 0.0);
+        if (z < g.n3 - 1) cf[ctr + 9] = mk(-inv_h2, 0.0);
+    }
+}
+
+__device__ __forceinline__ double p1(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+// coef_c[J][o] = sum_{i in supp P_J} P_iJ sum_t M[i][t] P_{i+t, J+o}
+__global__ void k_galerkin(Grid gf, Grid gc, const c128* __restrict__ cf, c128* __restrict__ cc) {
+    const int K = gf.dim == 3 ? 27 : 9;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= gc.N * K) return;
+    long long J = e / K;
+    int o = (int)(e - J * K);
+    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = gf.dim == 3 ? o / 9 - 1 : 0;
+    int jx, jy, jz;
+    gc.coords(J, jx, jy, jz);
+    int kx = jx + ox, ky = jy + oy, kz = jz + oz;   // coarse neighbour J + o
+    c128 acc = mk(0.0, 0.0);
+    if (kx >= 0 && kx < gc.n1 && ky >= 0 && ky < gc.n2 && kz >= 0 && kz < gc.n3) {
+        const int dzlo = gf.dim == 3 ? -1 : 0, dzhi = gf.dim == 3 ? 1 : 0;
+        for (int dz = dzlo; dz <= dzhi; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int ix = 2 * jx + dx, iy = 2 * jy + dy, iz = gf.dim == 3 ? 2 * jz + dz : 0;
+                    if (ix < 0 || ix >= gf.n1 || iy < 0 || iy >= gf.n2 || iz < 0 || iz >= gf.n3)
+                        continue;
+                    double wi = p1(dx) * p1(dy) * p1(dz);
+                    const c128* row = cf + gf.index(ix, iy, iz) * K;
+                    for (int tz = dzlo; tz <= dzhi; ++tz)
+                        for (int ty = -1; ty <= 1; ++ty)
+                            for (int tx = -1; tx <= 1; ++tx) {
+                                int fx = ix + tx, fy = iy + ty, fz = iz + tz;
+                                double wk = p1(fx - 2 * kx) * p1(fy - 2 * ky) *
+                                            (gf.dim == 3 ? p1(fz - 2 * kz) : 1.0);
+                                if (wk == 0.0) continue;
+                                if (fx < 0 || fx >= gf.n1 || fy < 0 || fy >= gf.n2 || fz < 0 ||
+                                    fz >= gf.n3)
+                                    continue;
+                                int t = (tx + 1) + 3 * (ty + 1) + (gf.dim == 3 ? 9 * (tz + 1) : 0);
+                                c128 mv = row[t];
+                                acc.re += wi * wk * mv.re;
+                                acc.im += wi * wk * mv.im;
+                            }
+                }
+    }
+    cc[e] = acc;
+}
+
+__global__ void k_diag_inv(Grid g, const c128* __restrict__ coef, c128* __restrict__ dinv) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const int K = g.dim == 3 ? 27 : 9;
+    c128 d = coef[i * K + (K / 2)];
+    double den = d.re * d.re + d.im * d.im;
+    dinv[i] = mk(d.re / den, -d.im / den);
+}
+
+__global__ void k_stencil_to_dense(Grid g, const c128* __restrict__ coef, c128* __restrict__ D) {
+    const int K = g.dim == 3 ? 27 : 9;
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= g.N * K) return;
+    long long i = e / K;
+    int o = (int)(e - i * K);
+    int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = g.dim == 3 ? o / 9 - 1 : 0;
+    int x, y, z;
+    g.coords(i, x, y, z);
+    x += ox; y += oy; z += oz;
+    if (x < 0 || x >= g.n1 || y < 0 || y >= g.n2 || z < 0 || z >= g.n3) return;
+    D[i * g.N + g.index(x, y, z)] = coef[e];
+}
+
+__global__ void k_aug_init(c128* aug, int n) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)n * n) return;
+    long long i = e / n, j = e - i * n;
+    aug[i * 2 * n + n + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+}
+
+// One block: pivot row p = argmax_{i>=k} |aug[i][k]|; factor[i] = entry of
+// column k in row i after the swap of rows k and p (factor[k] = 0).
+__global__ void __launch_bounds__(1024) k_gj_pivot(c128* aug, int n, int k, c128* factor, int* piv,
+                                                   c128* pivval, int* status) {
+    __shared__ double sval[1024];
+    __shared__ int sidx[1024];
+    const long long ld = 2LL * n;
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+        c128 a = aug[i * ld + k];
+        double v = a.re * a.re + a.im * a.im;
+        if (v > best) { best = v; bi = i; }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            double o = sval[threadIdx.x + w];
+            int oi = sidx[threadIdx.x + w];
+            if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+                sval[threadIdx.x] = o;
+                sidx[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    int p = sidx[0];
+    if (threadIdx.x == 0) {
+        *piv = p;
+        *pivval = aug[(long long)p * ld + k];
+        if (!(sval[0] > 0.0)) *status = 1;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        c128 v;
+        if (i == k) v = mk(0.0, 0.0);
+        else if (i == p) v = aug[(long long)k * ld + k];
+        else v = aug[(long long)i * ld + k];
+        factor[i] = v;
+    }
+}
+
+__global__ void k_gj_swap_scale(c128* aug, int n, int k, const int* piv, const c128* pivval) {
+    int j = k + blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 2 * n) return;
+    const long long ld = 2LL * n;
+    int p = *piv;
+    c128 pv = *pivval;
+    double den = pv.re * pv.re + pv.im * pv.im;
+    c128 inv = den > 0.0 ? mk(pv.re / den, -pv.im / den) : mk(0.0, 0.0);
+    c128 a = aug[(long long)k * ld + j];
+    c128 b = aug[(long long)p * ld + j];
+    if (p != k) aug[(long long)p * ld + j] = a;
+    aug[(long long)k * ld + j] = inv * b;
+}
+
+__global__ void k_gj_eliminate(c128* aug, int n, int k, const c128* __restrict__ factor) {
+    const long long ld = 2LL * n;
+    int j = k + blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.y;
+    if (j >= 2 * n || i == k) return;
+    c128 f = factor[i];
+    if (f.re == 0.0 && f.im == 0.0) return;
+    c128 rk = aug[(long long)k * ld + j];
+    c128 v = aug[(long long)i * ld + j];
+    aug[(long long)i * ld + j] = v - f * rk;
+}
+
+__global__ void k_extract_inverse(const c128* aug, int n, c128* out, c64* out32) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)n * n) return;
+    long long i = e / n, j = e - i * n;
+    c128 v = aug[i * 2 * n + n + j];
+    out[e] = v;
+    if (out32) out32[e] = cvt<float>(v);
+}
+
+__global__ void k_round_c64(const c128* in, c64* out, long long count) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < count) out[e] = cvt<float>(in[e]);
+}
+
+}  // namespace
+
+// ---------------- launchers ----------------
+//
+// Each launcher reports the launch's algorithmic traffic and flops to the
+// profiler: every vector element read or written once, coefficients once per
+// node, no cache effects.  E = N s elements; b* = bytes of one complex value.
+
+template <typename T>
+constexpr double cb() { return 2.0 * sizeof(T); }
+
+template <typename Op> struct OpCost;
+template <typename T> struct OpCost<FineOp<T>> {
+    static double coef_bytes(const FineOp<T>&) { return cb<T>(); }          // c per node
+    static double flops(const FineOp<T>& op) { return 4.0 * op.g.dim + 12.0; }
+    static constexpr bool fine = true;
+};
+template <typename T> struct OpCost<GalOp<T>> {
+    static double K(const GalOp<T>& op) { return op.g.dim == 3 ? 27.0 : 9.0; }
+    static double coef_bytes(const GalOp<T>& op) { return K(op) * cb<T>(); }
+    static double flops(const GalOp<T>& op) { return 8.0 * K(op); }
+    static constexpr bool fine = false;
+};
+
+template <typename T, typename U, typename V, typename Op>
+void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, int s) {
+    long long total = op.g.N * s;
+    L.pre(OpCost<Op>::fine ? KID_APPLY_FINE : KID_APPLY_COARSE,
+          total * (cb<U>() + cb<V>()) + op.g.N * OpCost<Op>::coef_bytes(op),
+          total * OpCost<Op>::flops(op));
+    k_apply<T, U, V, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, x, y, s, total);
+    L.post();
+}
+
+template <typename T, typename Op>
+void launch_residual(const Launch& L, const Op& op, const cplx<T>* x, const cplx<T>* b,
+                     cplx<T>* r, int s) {
+    long long total = op.g.N * s;
+    L.pre(KID_RESIDUAL, total * 3 * cb<T>() + op.g.N * OpCost<Op>::coef_bytes(op),
+          total * (OpCost<Op>::flops(op) + 2));
+    k_residual<T, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, x, b, r, s, total);
+    L.post();
+}
+
+template <typename T, typename FT, typename Op>
+void launch_jacobi(const Launch& L, const Op& op, const cplx<T>* u_in, const cplx<FT>* f,
+                   cplx<T>* u_out, int s, T w) {
+    long long total = op.g.N * s;
+    double bytes, flops;
+    if (u_in == nullptr) {
+        bytes = total * (cb<FT>() + cb<T>()) + op.g.N * cb<T>();
+        flops = total * 8.0;
+    } else {
+        bytes = total * (cb<FT>() + 2 * cb<T>()) + op.g.N * (OpCost<Op>::coef_bytes(op) + cb<T>());
+        flops = total * (OpCost<Op>::flops(op) + 12.0);
+    }
+    L.pre(OpCost<Op>::fine ? KID_JACOBI_FINE : KID_JACOBI_COARSE, bytes, flops);
+    k_jacobi<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, u_in, f, u_out, s, w, total);
+    L.post();
+}
+
+template <typename T, typename FT, typename Op>
+void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const cplx<T>* u,
+                           const cplx<FT>* f, cplx<T>* rc, int s) {
+    long long total = gc.N * s;
+    double ef = (double)op.g.N * s;
+    double bytes = ef * (cb<FT>() + (u ? cb<T>() : 0.0)) + total * cb<T>() +
+                   op.g.N * OpCost<Op>::coef_bytes(op);
+    double flops = ef * ((u ? OpCost<Op>::flops(op) : 0.0) + 2.0) + total * 2.0 * (op.g.dim == 3 ? 27 : 9);
+    L.pre(OpCost<Op>::fine ? KID_RESTRICT_FINE : KID_RESTRICT_COARSE, bytes, flops);
+    k_resid_restrict<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, gc, u, f, rc, s, total);
+    L.post();
+}
+
+template <typename T>
+void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const cplx<T>* ec,
+                        cplx<T>* u, int s) {
+    long long total = gf.N * s;
+    L.pre(KID_PROLONG, total * 2 * cb<T>() + (double)gc.N * s * cb<T>(),
+          total * 2.0 * (gf.dim == 3 ? 8 : 4));
+    k_prolong_add<T><<<blocks_for(total), kThreads, 0, L.st>>>(gf, gc, ec, u, s, total);
+    L.post();
+}
+
+template <typename T>
+void launch_dense_apply(const Launch& L, const cplx<T>* Minv, int n, const cplx<T>* f, cplx<T>* u,
+                        int s) {
+    dim3 grid((s + 31) / 32, (n + 31) / 32);
+    L.pre(KID_DENSE, (double)n * n * cb<T>() + 2.0 * n * s * cb<T>(), 8.0 * n * (double)n * s);
+    k_dense_apply<T><<<grid, 256, 0, L.st>>>(Minv, n, f, u, s);
+    L.post();
+}
+
+void launch_fine_setup(const Launch& L, const Grid& g, const double* m, const double* gamma,
+                       double omega, double shift, double inv_h2, c128* cA, c128* cM,
+                       c128* dinvM, c128* coefM) {
+    L.pre(KID_SETUP, 0, 0);
+    k_fine_setup<<<blocks_for(g.N), kThreads, 0, L.st>>>(g, m, gamma, omega, shift, inv_h2, cA, cM,
+                                                         dinvM, coefM);
+    L.post();
+}
+
+void launch_galerkin(const Launch& L, const Grid& gf, const Grid& gc, const c128* coef_f,
+                     c128* coef_c) {
+    const int K = gf.dim == 3 ? 27 : 9;
+    L.pre(KID_SETUP, 0, 0);
+    k_galerkin<<<blocks_for(gc.N * K), kThreads, 0, L.st>>>(gf, gc, coef_f, coef_c);
+    L.post();
+}
+
+void launch_diag_inv(const Launch& L, const Grid& g, const c128* coef, c128* dinv) {
+    L.pre(KID_SETUP, 0, 0);
+    k_diag_inv<<<blocks_for(g.N), kThreads, 0, L.st>>>(g, coef, dinv);
+    L.post();
+}
+
+void launch_stencil_to_dense(const Launch& L, const Grid& g, const c128* coef, c128* dense) {
+    const int K = g.dim == 3 ? 27 : 9;
+    cudaMemsetAsync(dense, 0, sizeof(c128) * g.N * g.N, L.st);
+    L.pre(KID_SETUP, 0, 0);
+    k_stencil_to_dense<<<blocks_for(g.N * K), kThreads, 0, L.st>>>(g, coef, dense);
+    L.post();
+}
+
+void launch_gauss_jordan(const Launch& L, c128* aug, int n, c128* factor, int* piv, c128* pivval,
+                         int* status) {
+    L.pre(KID_SETUP, 0, 0);
+    k_aug_init<<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(aug, n);
+    L.post();
+    for (int k = 0; k < n; ++k) {
+        L.pre(KID_SETUP, 0, 0);
+        k_gj_pivot<<<1, 1024, 0, L.st>>>(aug, n, k, factor, piv, pivval, status);
+        L.post();
+        int cols = 2 * n - k;
+        L.pre(KID_SETUP, 0, 0);
+        k_gj_swap_scale<<<(cols + 255) / 256, 256, 0, L.st>>>(aug, n, k, piv, pivval);
+        L.post();
+        dim3 grid((cols + 255) / 256, n);
+        L.pre(KID_SETUP, 0, 0);
+        k_gj_eliminate<<<grid, 256, 0, L.st>>>(aug, n, k, factor);
+        L.post();
+    }
+}
+
+void launch_extract_inverse(const Launch& L, const c128* aug, int n, c128* out, c64* out32) {
+    L.pre(KID_SETUP, 0, 0);
+    k_extract_inverse<<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(aug, n, out, out32);
+    L.post();
+}
+
+void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count) {
+    L.pre(KID_LAYOUT, count * (16.0 + 8.0), 0);
+    k_round_c64<<<blocks_for(count), kThreads, 0, L.st>>>(in, out, count);
+    L.post();
+}
+
+// ---------------- explicit instantiations ----------------
+
+#define HELM_INST_T(T)                                                                           \
+    template void launch_apply<T, T, T, FineOp<T>>(const Launch&, const FineOp<T>&,              \
+                                                   const cplx<T>*, cplx<T>*, int);               \
+    template void launch_apply<T, T, T, GalOp<T>>(const Launch&, const GalOp<T>&,                \
+                                                  const cplx<T>*, cplx<T>*, int);                \
+    template void launch_residual<T, FineOp<T>>(const Launch&, const FineOp<T>&, const cplx<T>*, \
+                                                const cplx<T>*, cplx<T>*, int);                  \
+    template void launch_jacobi<T, T, FineOp<T>>(const Launch&, const FineOp<T>&,                \
+                                                 const cplx<T>*, const cplx<T>*, cplx<T>*, int,  \
+                                                 T);                                             \
+    template void launch_jacobi<T, T, GalOp<T>>(const Launch&, const GalOp<T>&, const cplx<T>*,  \
+                                                const cplx<T>*, cplx<T>*, int, T);               \
+    template void launch_resid_restrict<T, T, FineOp<T>>(const Launch&, const FineOp<T>&,        \
+                                                         const Grid&, const cplx<T>*,            \
+                                                         const cplx<T>*, cplx<T>*, int);         \
+    template void launch_resid_restrict<T, T, GalOp<T>>(const Launch&, const GalOp<T>&,          \
+                                                        const Grid&, const cplx<T>*,             \
+                                                        const cplx<T>*, cplx<T>*, int);          \
+    template void launch_prolong_add<T>(const Launch&, const Grid&, const Grid&, const cplx<T>*, \
+                                        cplx<T>*, int);                                          \
+    template void launch_dense_apply<T>(const Launch&, const cplx<T>*, int, const cplx<T>*,      \
+                                        cplx<T>*, int);
+
+HELM_INST_T(float)
+HELM_INST_T(double)
+// complex64 cycle fed by a complex128 right-hand side (the Krylov basis)
+template void launch_jacobi<float, double, FineOp<float>>(const Launch&, const FineOp<float>&,
+                                                          const cplx<float>*, const cplx<double>*,
+                                                          cplx<float>*, int, float);
+template void launch_jacobi<float, double, GalOp<float>>(const Launch&, const GalOp<float>&,
+                                                         const cplx<float>*, const cplx<double>*,
+                                                         cplx<float>*, int, float);
+template void launch_resid_restrict<float, double, FineOp<float>>(const Launch&,
+                                                                  const FineOp<float>&,
+                                                                  const Grid&, const cplx<float>*,
+                                                                  const cplx<double>*,
+                                                                  cplx<float>*, int);
+template void launch_resid_restrict<float, double, GalOp<float>>(const Launch&,
+                                                                 const GalOp<float>&, const Grid&,
+                                                                 const cplx<float>*,
+                                                                 const cplx<double>*,
+                                                                 cplx<float>*, int);
+// outer A Z with Z in complex64, W in complex128 (FP64 arithmetic)
+template void launch_apply<double, float, double, FineOp<double>>(const Launch&,
+                                                                  const FineOp<double>&,
+                                                                  const cplx<float>*,
+                                                                  cplx<double>*, int);
+
+}  // namespace helm

@@ -1,0 +1,1133 @@
+// libhelm host driver: set-up of the shifted-Laplacian hierarchy, the
+// multigrid cycle and block FGMRES (Sec. 4 and Sec. 5.3 of Treister & Haber),
+// behind the C-ABI declared in include/helm.h.
+//
+// Work split: every N-sized step (stencils, transfers, coarsest solve, Gram
+// products, block updates, norms, layout changes) runs in the kernels of
+// mg.cu / krylov.cu on the context's stream; the host keeps only the
+// block-sized dense algebra of the Krylov method (s_b x s_b Cholesky factors
+// and the block-Hessenberg least-squares problem, a few kB), in FP64.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/helm.h"
+#include "kernels.h"
+
+using helm::c128;
+using helm::c64;
+using helm::cplx;
+using helm::Grid;
+using helm::Launch;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+// A block column is dependent when its part orthogonal to the columns before
+// it has a sine below kDepAngle, or is below kDepRoundoff times the column's
+// norm before any orthogonalisation (same reading as the oracle).
+constexpr double kDepAngle = 1e-7;
+constexpr double kDepRoundoff = 1e-12;
+
+struct Level {
+    Grid g;
+    c128* coef = nullptr;    // K-point stencil of M_l (FP64)
+    c128* dinv = nullptr;    // Jacobi inverse diagonal of M_l (FP64)
+    c64* coef32 = nullptr;
+    c64* dinv32 = nullptr;
+    // cycle work buffers, N_l x s_cap complex128-sized (complex64 uses half)
+    void* u0 = nullptr;
+    void* u1 = nullptr;
+    void* e = nullptr;       // coarse-level solution (levels >= 1)
+    void* f = nullptr;       // coarse-level right-hand side (levels >= 1)
+};
+
+}  // namespace
+
+// Per-launch CUDA-event profiler (enabled by helm_profile_enable): every
+// launcher records an event pair around its kernel on the context's stream,
+// with the launch's algorithmic bytes and flops; helm_profile_read resolves
+// the pairs and accumulates per kernel class.
+namespace helm {
+struct Profiler {
+    struct Rec { int kid; double bytes, flops; cudaEvent_t a, b; };
+    std::vector<Rec> open;
+    std::vector<cudaEvent_t> pool;
+    double time_ms[KID_COUNT] = {};
+    double bytes[KID_COUNT] = {};
+    double flops[KID_COUNT] = {};
+    long long launches[KID_COUNT] = {};
+
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void resolve() {
+        for (auto& r : open) {
+            cudaEventSynchronize(r.b);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, r.a, r.b);
+            time_ms[r.kid] += ms;
+            bytes[r.kid] += r.bytes;
+            flops[r.kid] += r.flops;
+            launches[r.kid] += 1;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        open.clear();
+    }
+    void reset() {
+        resolve();
+        for (int k = 0; k < KID_COUNT; ++k) time_ms[k] = bytes[k] = flops[k] = 0, launches[k] = 0;
+    }
+    ~Profiler() {
+        resolve();
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+void prof_begin(Profiler* p, cudaStream_t st, int kid, double bytes, double flops) {
+    Profiler::Rec r{kid, bytes, flops, p->get(), p->get()};
+    cudaEventRecord(r.a, st);
+    p->open.push_back(r);
+    if (p->open.size() > 4096) {  // bound the number of events in flight
+        cudaEventRecord(r.b, st);
+        p->open.back().b = r.b;
+    }
+}
+
+void prof_end(Profiler* p, cudaStream_t st) {
+    if (p->open.empty()) return;
+    cudaEventRecord(p->open.back().b, st);
+    if (p->open.size() > 4096) p->resolve();
+}
+}  // namespace helm
+
+struct helm_ctx {
+    helm_params p{};
+    cudaStream_t st = nullptr;
+    long long launches = 0;
+    std::string err;
+    double inv_h2 = 0;
+    std::vector<Level> lv;
+    // fine-level mass coefficients of A and M
+    c128* cA = nullptr;
+    c128* cM = nullptr;
+    c64* cA32 = nullptr;
+    c64* cM32 = nullptr;
+    // coarsest inverse
+    int nc = 0;
+    c128* Minv = nullptr;
+    c64* Minv32 = nullptr;
+    // Krylov workspace, sized for s_cap columns
+    int s_cap = 0;
+    c128* V = nullptr;       // (restart+1) blocks of N x s
+    void* Z = nullptr;       // restart blocks (complex128 or complex64)
+    c128* W = nullptr;
+    c128* W2 = nullptr;
+    c128* Bint = nullptr;
+    c128* X = nullptr;
+    c128* R = nullptr;
+    c128* abi_in = nullptr;  // device staging for helm_solve_host
+    c128* abi_out = nullptr;
+    c128* partial = nullptr;
+    long long partial_elems = 0;
+    c128* small = nullptr;   // device small matrices (H passes, G, T, Y)
+    long long small_elems = 0;
+    int* dmask = nullptr;
+    c128* hsmall = nullptr;  // pinned host mirror of `small`
+    unsigned long long rng_counter = 0x5eed;
+    helm::Profiler* prof = nullptr;
+
+    Launch L() { return Launch{st, &launches, prof}; }
+    long long N() const { return lv[0].g.N; }
+};
+
+namespace {
+
+helm_status fail(helm_ctx* c, helm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    g_thread_error = msg;
+    return s;
+}
+
+#define CUDA_TRY(ctx, expr)                                                            \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA, \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(P** p, size_t bytes) {
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+
+template <typename T> const cplx<T>* pick(const c128* d, const c64* f);
+template <> const cplx<double>* pick<double>(const c128* d, const c64*) { return d; }
+template <> const cplx<float>* pick<float>(const c128*, const c64* f) { return f; }
+
+template <typename T>
+helm::FineOp<T> fine_op(const helm_ctx* c, bool shifted) {
+    helm::FineOp<T> op;
+    op.g = c->lv[0].g;
+    op.inv_h2 = (T)c->inv_h2;
+    op.c = shifted ? pick<T>(c->cM, c->cM32) : pick<T>(c->cA, c->cA32);
+    op.dinv = pick<T>(c->lv[0].dinv, c->lv[0].dinv32);
+    return op;
+}
+
+template <typename T>
+helm::GalOp<T> gal_op(const helm_ctx* c, int l) {
+    helm::GalOp<T> op;
+    op.g = c->lv[l].g;
+    op.coef = pick<T>(c->lv[l].coef, c->lv[l].coef32);
+    op.dinv = pick<T>(c->lv[l].dinv, c->lv[l].dinv32);
+    return op;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid cycle (Alg. "Two-grid cycle", applied recursively = V-cycle)
+// ---------------------------------------------------------------------------
+
+template <typename T, typename FT>
+void smooth_level(helm_ctx* c, int l, const cplx<T>* uin, const cplx<FT>* f, cplx<T>* uout,
+                  int s) {
+    T w = (T)c->p.jacobi_w;
+    if (l == 0)
+        helm::launch_jacobi<T, FT, helm::FineOp<T>>(c->L(), fine_op<T>(c, true), uin, f, uout, s, w);
+    else
+        helm::launch_jacobi<T, FT, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), uin, f, uout, s, w);
+}
+
+template <typename T, typename FT>
+void restrict_level(helm_ctx* c, int l, const cplx<T>* u, const cplx<FT>* f, cplx<T>* rc, int s) {
+    if (l == 0)
+        helm::launch_resid_restrict<T, FT, helm::FineOp<T>>(c->L(), fine_op<T>(c, true),
+                                                            c->lv[1].g, u, f, rc, s);
+    else
+        helm::launch_resid_restrict<T, FT, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), c->lv[l + 1].g,
+                                                           u, f, rc, s);
+}
+
+template <typename T>
+void coarsest(helm_ctx* c, const cplx<T>* f, cplx<T>* u, int s) {
+    helm::launch_dense_apply<T>(c->L(), pick<T>(c->Minv, c->Minv32), c->nc, f, u, s);
+}
+
+// out = cycle(f) on level l with zero initial guess.  `out` must not alias the
+// level's own work buffers.
+template <typename T, typename FT>
+void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
+    const int Lv = (int)c->lv.size();
+    Level& lev = c->lv[l];
+    if (l == Lv - 1) {
+        if constexpr (std::is_same<T, FT>::value) {
+            coarsest<T>(c, f, out, s);
+        } else {
+            // one-level hierarchy with a complex128 right-hand side: round it first
+            cplx<T>* tmp = reinterpret_cast<cplx<T>*>(lev.u0);
+            helm::launch_round_c64(c->L(), reinterpret_cast<const c128*>(f),
+                                   reinterpret_cast<c64*>(tmp), lev.g.N * (long long)s);
+            coarsest<T>(c, tmp, out, s);
+        }
+        return;
+    }
+    cplx<T>* bufA = reinterpret_cast<cplx<T>*>(lev.u0);
+    cplx<T>* bufB = reinterpret_cast<cplx<T>*>(lev.u1);
+    const cplx<T>* cur = nullptr;
+    for (int k = 0; k < c->p.pre; ++k) {
+        cplx<T>* dst = (k % 2 == 0) ? bufA : bufB;
+        smooth_level<T, FT>(c, l, cur, f, dst, s);
+        cur = dst;
+    }
+    Level& nxt = c->lv[l + 1];
+    cplx<T>* fc = reinterpret_cast<cplx<T>*>(nxt.f);
+    cplx<T>* ec = reinterpret_cast<cplx<T>*>(nxt.e);
+    restrict_level<T, FT>(c, l, cur, f, fc, s);
+    cycle<T, T>(c, l + 1, fc, ec, s);
+    cplx<T>* u = const_cast<cplx<T>*>(cur);
+    if (u == nullptr) {
+        u = bufA;
+        helm::launch_zero(c->L(), u, sizeof(cplx<T>) * lev.g.N * s);
+    }
+    helm::launch_prolong_add<T>(c->L(), lev.g, nxt.g, ec, u, s);
+    cur = u;
+    if (c->p.post == 0) {
+        cudaMemcpyAsync(out, cur, sizeof(cplx<T>) * lev.g.N * s, cudaMemcpyDeviceToDevice, c->st);
+        return;
+    }
+    for (int k = 0; k < c->p.post; ++k) {
+        cplx<T>* dst = (k == c->p.post - 1) ? out : (cur == bufA ? bufB : bufA);
+        smooth_level<T, FT>(c, l, cur, f, dst, s);
+        cur = dst;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+void free_workspace(helm_ctx* c) {
+    for (auto& l : c->lv) {
+        dfree(l.u0); dfree(l.u1); dfree(l.e); dfree(l.f);
+        l.u0 = l.u1 = l.e = l.f = nullptr;
+    }
+    dfree(c->V); dfree(c->Z); dfree(c->W); dfree(c->W2); dfree(c->Bint); dfree(c->X);
+    dfree(c->R); dfree(c->abi_in); dfree(c->abi_out); dfree(c->partial); dfree(c->small);
+    dfree(c->dmask);
+    if (c->hsmall) cudaFreeHost(c->hsmall);
+    c->V = c->W = c->W2 = c->Bint = c->X = c->R = c->abi_in = c->abi_out = c->partial = c->small =
+        nullptr;
+    c->Z = nullptr;
+    c->dmask = nullptr;
+    c->hsmall = nullptr;
+    c->s_cap = 0;
+}
+
+helm_status ensure_workspace(helm_ctx* c, int s) {
+    if (s <= c->s_cap) return HELM_OK;
+    free_workspace(c);
+    const long long N = c->N();
+    const size_t vec = sizeof(c128) * (size_t)N * s;
+    const int m = c->p.restart;
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        size_t b = sizeof(c128) * (size_t)c->lv[l].g.N * s;
+        CUDA_TRY(c, dalloc(&c->lv[l].u0, b));
+        CUDA_TRY(c, dalloc(&c->lv[l].u1, b));
+        if (l > 0) {
+            CUDA_TRY(c, dalloc(&c->lv[l].e, b));
+            CUDA_TRY(c, dalloc(&c->lv[l].f, b));
+        }
+    }
+    const size_t zel = c->p.prec == HELM_PLAIN_C128 ? sizeof(c128) : sizeof(c64);
+    CUDA_TRY(c, dalloc(&c->V, vec * (m + 1)));
+    CUDA_TRY(c, dalloc(&c->Z, zel * (size_t)N * s * m));
+    CUDA_TRY(c, dalloc(&c->W, vec));
+    CUDA_TRY(c, dalloc(&c->W2, vec));
+    CUDA_TRY(c, dalloc(&c->Bint, vec));
+    CUDA_TRY(c, dalloc(&c->X, vec));
+    CUDA_TRY(c, dalloc(&c->R, vec));
+    const int sb = std::min(c->p.block, s);
+    const int G = (s + sb - 1) / sb;
+    long long pe = std::max(helm::gram_partial_elems(N, m + 1, s, sb),
+                            helm::colnorm_partial_elems(N, s));
+    pe = std::max(pe, helm::gram_partial_elems(N, 1, s, sb));
+    c->partial_elems = pe;
+    CUDA_TRY(c, dalloc(&c->partial, sizeof(c128) * pe));
+    // small: 2 H passes + G + T + Y + norms
+    long long blk = (long long)G * sb * sb;
+    c->small_elems = 2 * (m + 1) * blk + 2 * blk + (long long)m * blk + 4LL * s + 64;
+    CUDA_TRY(c, dalloc(&c->small, sizeof(c128) * c->small_elems));
+    CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->hsmall), sizeof(c128) * c->small_elems));
+    CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
+    c->s_cap = s;
+    return HELM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small dense algebra on the host (FP64)
+// ---------------------------------------------------------------------------
+
+// Cholesky of one group's Gram matrix G (n x n, row-major, Hermitian) with the
+// dependence test; R upper triangular (row-major), T = R^{-1} on the
+// independent columns (zero rows/columns for dependent ones).
+bool chol_dep(const cd* G, const double* ref2, int n, std::vector<cd>& R, std::vector<cd>& T,
+              std::vector<int>& dep, bool allow_dep) {
+    R.assign((size_t)n * n, 0.0);
+    T.assign((size_t)n * n, 0.0);
+    dep.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+        double gkk = G[k * n + k].real();
+        double d = gkk;
+        for (int i = 0; i < k; ++i) d -= std::norm(R[i * n + k]);
+        bool dependent = !(gkk > 0.0) || !(d > kDepAngle * kDepAngle * gkk) ||
+                         (ref2 && !(d > kDepRoundoff * kDepRoundoff * ref2[k]));
+        if (dependent) {
+            if (!allow_dep) return false;
+            dep[k] = 1;
+            continue;
+        }
+        double rkk = std::sqrt(d);
+        R[k * n + k] = rkk;
+        for (int l = k + 1; l < n; ++l) {
+            cd v = G[k * n + l];
+            for (int i = 0; i < k; ++i) v -= std::conj(R[i * n + k]) * R[i * n + l];
+            R[k * n + l] = v / rkk;
+        }
+    }
+    // T = R^{-1} restricted to the independent index set
+    for (int l = 0; l < n; ++l) {
+        if (dep[l]) continue;
+        T[l * n + l] = 1.0 / R[l * n + l];
+        for (int i = l - 1; i >= 0; --i) {
+            if (dep[i]) continue;
+            cd v = 0.0;
+            for (int t = i + 1; t <= l; ++t)
+                if (!dep[t]) v += R[i * n + t] * T[t * n + l];
+            T[i * n + l] = -v / R[i * n + i];
+        }
+    }
+    return true;
+}
+
+// Incrementally QR-factorised block Hessenberg least-squares problem of one
+// group: min_Y || E_1 Lambda - Hbar_j Y ||_F, by Householder reflections
+// applied to each new block column as it arrives.
+struct BlockLS {
+    int sb = 0, m = 0;
+    int rows = 0;                      // (m+1) sb
+    std::vector<cd> Rm;                // rows x (m sb), column-major
+    std::vector<cd> gv;                // rows x sb, column-major
+    std::vector<std::vector<cd>> refl; // per step: sb vectors of length 2 sb
+    std::vector<std::vector<double>> beta;
+
+    void init(int sb_, int m_, const std::vector<cd>& Lam /* sb x sb row-major */) {
+        sb = sb_; m = m_; rows = (m + 1) * sb;
+        Rm.assign((size_t)rows * m * sb, 0.0);
+        gv.assign((size_t)rows * sb, 0.0);
+        for (int a = 0; a < sb; ++a)
+            for (int b = 0; b < sb; ++b) gv[(size_t)b * rows + a] = Lam[a * sb + b];
+        refl.assign(m, {});
+        beta.assign(m, {});
+    }
+
+    static void apply_refl(const cd* v, double bt, int len, cd* y) {
+        if (bt == 0.0) return;
+        cd d = 0.0;
+        for (int t = 0; t < len; ++t) d += std::conj(v[t]) * y[t];
+        d *= bt;
+        for (int t = 0; t < len; ++t) y[t] -= v[t] * d;
+    }
+
+    // hcol: (j+2) sb x sb, column-major with leading dimension `ld`.
+    // Returns per-column residual estimates.
+    std::vector<double> add(int j, std::vector<cd>& hcol, int ld) {
+        const int L2 = 2 * sb;
+        for (int i = 0; i < j; ++i)
+            for (int c = 0; c < sb; ++c)
+                for (int q = 0; q < sb; ++q)
+                    apply_refl(&refl[i][(size_t)q * L2], beta[i][q], L2, &hcol[(size_t)c * ld + i * sb]);
+        refl[j].assign((size_t)sb * L2, 0.0);
+        beta[j].assign(sb, 0.0);
+        for (int q = 0; q < sb; ++q) {
+            cd* x = &hcol[(size_t)q * ld + j * sb];  // rows j sb .. j sb + 2sb - 1 of column q
+            double nrm2 = 0;
+            for (int t = q; t < L2; ++t) nrm2 += std::norm(x[t]);
+            double nrm = std::sqrt(nrm2);
+            cd* v = &refl[j][(size_t)q * L2];
+            if (nrm == 0.0) { beta[j][q] = 0.0; continue; }
+            cd x0 = x[q];
+            cd alpha = (std::abs(x0) > 0) ? -x0 / std::abs(x0) * nrm : cd(-nrm, 0.0);
+            for (int t = q; t < L2; ++t) v[t] = x[t];
+            v[q] -= alpha;
+            double vn2 = 0;
+            for (int t = q; t < L2; ++t) vn2 += std::norm(v[t]);
+            beta[j][q] = vn2 > 0 ? 2.0 / vn2 : 0.0;
+            for (int c = q; c < sb; ++c) apply_refl(v, beta[j][q], L2, &hcol[(size_t)c * ld + j * sb]);
+        }
+        for (int c = 0; c < sb; ++c)
+            for (int q = 0; q < sb; ++q)
+                apply_refl(&refl[j][(size_t)q * L2], beta[j][q], L2, &gv[(size_t)c * rows + j * sb]);
+        for (int c = 0; c < sb; ++c)
+            for (int r = 0; r < (j + 1) * sb; ++r)
+                Rm[(size_t)(j * sb + c) * rows + r] = hcol[(size_t)c * ld + r];
+        std::vector<double> est(sb);
+        for (int c = 0; c < sb; ++c) {
+            double e2 = 0;
+            for (int r = (j + 1) * sb; r < (j + 2) * sb; ++r) e2 += std::norm(gv[(size_t)c * rows + r]);
+            est[c] = std::sqrt(e2);
+        }
+        return est;
+    }
+
+    // Y ((j+1) sb x sb, row-major [row][col]) from the first j+1 block steps.
+    std::vector<cd> solve(int j) const {
+        const int n = (j + 1) * sb;
+        std::vector<cd> Y((size_t)n * sb, 0.0);
+        double dmax = 0;
+        for (int r = 0; r < n; ++r) dmax = std::max(dmax, std::abs(Rm[(size_t)r * rows + r]));
+        for (int c = 0; c < sb; ++c)
+            for (int r = n - 1; r >= 0; --r) {
+                cd v = gv[(size_t)c * rows + r];
+                for (int t = r + 1; t < n; ++t) v -= Rm[(size_t)t * rows + r] * Y[(size_t)t * sb + c];
+                cd d = Rm[(size_t)r * rows + r];
+                Y[(size_t)r * sb + c] = (std::abs(d) > 1e-14 * dmax) ? v / d : cd(0.0);
+            }
+        return Y;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// block QR (CholQR2 with the dependence rule) of W against the basis V_0..V_{nb-1}
+// ---------------------------------------------------------------------------
+
+struct QRResult {
+    std::vector<std::vector<cd>> R;  // per group, sb x sb row-major
+};
+
+helm_status sync(helm_ctx* c) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    CUDA_TRY(c, cudaGetLastError());
+    return HELM_OK;
+}
+
+// Layout of c->small (elements of c128):
+//   [0, 2*(m+1)*blk)        H of the two Gram-Schmidt passes
+//   [oG, oG+blk)            Gram of the block being factorised
+//   [oT, oT+blk)            T factors uploaded by the host
+//   [oY, oY+m*blk)          least-squares solutions Y
+//   [oN, oN+4s)             column norms
+struct SmallLayout {
+    long long blk, oH1, oH2, oG, oT, oY, oN;
+};
+
+SmallLayout small_layout(const helm_ctx* c, int s, int sb) {
+    SmallLayout L;
+    int G = (s + sb - 1) / sb;
+    L.blk = (long long)G * sb * sb;
+    L.oH1 = 0;
+    L.oH2 = (long long)(c->p.restart + 1) * L.blk;
+    L.oG = 2 * L.oH2;
+    L.oT = L.oG + L.blk;
+    L.oY = L.oT + L.blk;
+    L.oN = L.oY + (long long)c->p.restart * L.blk;
+    return L;
+}
+
+// Gram-Schmidt (two passes) of the block at `W` against V_0..V_{nb-1};
+// H1/H2 receive the coefficients of the passes when non-null.
+void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
+    const long long N = c->N();
+    const long long vs = N * s;
+    for (int pass = 0; pass < 2; ++pass) {
+        c128* H = pass == 0 ? H1 : H2;
+        helm::launch_gram(c->L(), c->V, nb, vs, Wp, N, s, sb, c->partial, H);
+        helm::launch_combine<double>(c->L(), Wp, 1.0, -1.0, c->V, nb, vs, H, N, s, sb);
+    }
+}
+
+// Factor the block at Win (already orthogonal to V_0..V_{nb-1}) as Vout R.
+// extra2: per column, the squared norm removed by that orthogonalisation
+// (sum of |H_ik|^2), so that extra2 + ||W_k||^2 is the column's squared norm
+// before it.  Win is left unchanged.
+helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
+                     const std::vector<double>& extra2, QRResult& out, bool& any_dep) {
+    const long long N = c->N();
+    const int G = (s + sb - 1) / sb;
+    SmallLayout SL = small_layout(c, s, sb);
+    c128* dG = c->small + SL.oG;
+    c128* dT = c->small + SL.oT;
+    cd* hG = reinterpret_cast<cd*>(c->hsmall + SL.oG);
+    cd* hT = reinterpret_cast<cd*>(c->hsmall + SL.oT);
+    any_dep = false;
+    out.R.assign(G, {});
+    std::vector<std::vector<cd>> R1(G), R2(G);
+    std::vector<int> mask(s, 0);
+    // pass 1
+    helm::launch_gram(c->L(), Win, 1, 0, Win, N, s, sb, c->partial, dG);
+    CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
+    helm_status st = sync(c);
+    if (st != HELM_OK) return st;
+    for (int g = 0; g < G; ++g) {
+        const int n = std::min(sb, s - g * sb);
+        std::vector<cd> Gg((size_t)n * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) Gg[a * n + b] = hG[(size_t)g * sb * sb + a * sb + b];
+        for (int a = 0; a < n * n; ++a)
+            if (!std::isfinite(Gg[a].real()) || !std::isfinite(Gg[a].imag()))
+                return fail(c, HELM_ERR_NONFINITE, "non-finite value in the Krylov block");
+        std::vector<double> ref2(n);
+        for (int k = 0; k < n; ++k) ref2[k] = extra2[g * sb + k] + Gg[k * n + k].real();
+        std::vector<cd> T;
+        std::vector<int> dep;
+        chol_dep(Gg.data(), ref2.data(), n, R1[g], T, dep, true);
+        for (int a = 0; a < sb; ++a)
+            for (int b = 0; b < sb; ++b)
+                hT[(size_t)g * sb * sb + a * sb + b] = (a < n && b < n) ? T[a * n + b] : cd(0.0);
+        for (int k = 0; k < n; ++k)
+            if (dep[k]) { mask[g * sb + k] = 1; any_dep = true; }
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
+    helm::launch_combine<double>(c->L(), c->W2, 0.0, 1.0, Win, 1, 0, dT, N, s, sb);
+    if (any_dep) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->dmask, mask.data(), sizeof(int) * s, cudaMemcpyHostToDevice,
+                                    c->st));
+        helm::launch_fill_random(c->L(), c->W2, N, s, c->dmask, c->rng_counter++);
+        if (nb > 0) {
+            c128* Hs = c->small + SL.oT;  // scratch; T already consumed
+            cgs2(c, c->W2, nb, s, sb, Hs, Hs);
+        }
+    }
+    // pass 2
+    helm::launch_gram(c->L(), c->W2, 1, 0, c->W2, N, s, sb, c->partial, dG);
+    CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
+    st = sync(c);
+    if (st != HELM_OK) return st;
+    for (int g = 0; g < G; ++g) {
+        const int n = std::min(sb, s - g * sb);
+        std::vector<cd> Gg((size_t)n * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) Gg[a * n + b] = hG[(size_t)g * sb * sb + a * sb + b];
+        std::vector<cd> T;
+        std::vector<int> dep;
+        if (!chol_dep(Gg.data(), nullptr, n, R2[g], T, dep, false))
+            return fail(c, HELM_ERR_BREAKDOWN, "block QR: second Cholesky pass failed");
+        for (int a = 0; a < sb; ++a)
+            for (int b = 0; b < sb; ++b)
+                hT[(size_t)g * sb * sb + a * sb + b] = (a < n && b < n) ? T[a * n + b] : cd(0.0);
+        // R = R2 R1
+        std::vector<cd> Rg((size_t)sb * sb, 0.0);
+        for (int a = 0; a < n; ++a)
+            for (int b = a; b < n; ++b) {
+                cd v = 0.0;
+                for (int t = a; t <= b; ++t) v += R2[g][a * n + t] * R1[g][t * n + b];
+                Rg[a * sb + b] = v;
+            }
+        out.R[g] = Rg;
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
+    helm::launch_combine<double>(c->L(), Vout, 0.0, 1.0, c->W2, 1, 0, dT, N, s, sb);
+    return HELM_OK;
+}
+
+// per-column squared norms of an internal block (FP64), to host
+helm_status colnorms(helm_ctx* c, const c128* X, int s, std::vector<double>& out) {
+    SmallLayout SL = small_layout(c, s, std::min(c->p.block, s));
+    c128* d = c->small + SL.oN;
+    helm::launch_colnorm2(c->L(), X, c->N(), s, reinterpret_cast<double*>(c->partial),
+                          reinterpret_cast<double*>(d));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hsmall + SL.oN, d, sizeof(c128) * s, cudaMemcpyDeviceToHost, c->st));
+    helm_status st = sync(c);
+    if (st != HELM_OK) return st;
+    out.resize(s);
+    for (int j = 0; j < s; ++j) out[j] = c->hsmall[SL.oN + j].re;
+    return HELM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// block FGMRES (Sec. 5.3)
+// ---------------------------------------------------------------------------
+
+template <typename ZT>
+helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
+    const long long N = c->N();
+    const long long vs = N * s;
+    const int m = c->p.restart;
+    const int sb = std::min(c->p.block, s);
+    const int G = (s + sb - 1) / sb;
+    SmallLayout SL = small_layout(c, s, sb);
+    cplx<ZT>* Z = reinterpret_cast<cplx<ZT>*>(c->Z);
+    helm::FineOp<double> opA = fine_op<double>(c, false);
+
+    std::vector<double> bn2;
+    helm_status st = colnorms(c, c->Bint, s, bn2);
+    if (st != HELM_OK) return st;
+    std::vector<double> bn(s);
+    for (int j = 0; j < s; ++j) {
+        if (!std::isfinite(bn2[j])) return fail(c, HELM_ERR_NONFINITE, "non-finite right-hand side");
+        bn[j] = std::sqrt(bn2[j]);
+    }
+    helm::launch_zero(c->L(), c->X, sizeof(c128) * vs);
+    std::vector<int> iters(G, 0);
+    std::vector<char> done(G, 0);
+    std::vector<double> rel(s, 0.0);
+    helm_status result = HELM_NOT_CONVERGED;
+
+    for (int cyc = 0; cyc <= c->p.max_restarts; ++cyc) {
+        // true residual R = B - A X in FP64
+        if (cyc == 0)
+            CUDA_TRY(c, cudaMemcpyAsync(c->R, c->Bint, sizeof(c128) * vs, cudaMemcpyDeviceToDevice, c->st));
+        else
+            helm::launch_residual<double, helm::FineOp<double>>(c->L(), opA, c->X, c->Bint, c->R, s);
+        std::vector<double> rn2;
+        st = colnorms(c, c->R, s, rn2);
+        if (st != HELM_OK) return st;
+        bool all = true;
+        for (int j = 0; j < s; ++j) {
+            if (!std::isfinite(rn2[j])) {
+                result = fail(c, HELM_ERR_NONFINITE, "non-finite residual");
+                goto finish;
+            }
+            rel[j] = bn[j] > 0 ? std::sqrt(rn2[j]) / bn[j] : 0.0;
+        }
+        for (int g = 0; g < G; ++g) {
+            bool ok = true;
+            for (int j = g * sb; j < std::min(s, (g + 1) * sb); ++j) ok = ok && rel[j] <= tol;
+            done[g] = ok;
+            all = all && ok;
+        }
+        if (all) { result = HELM_OK; break; }
+        if (cyc == c->p.max_restarts) { result = HELM_NOT_CONVERGED; break; }
+
+        // V_0 Lambda = R
+        QRResult qr;
+        bool dep;
+        st = block_qr(c, c->R, c->V, 0, s, sb, std::vector<double>(s, 0.0), qr, dep);
+        if (st != HELM_OK) return st;
+        std::vector<BlockLS> ls(G);
+        for (int g = 0; g < G; ++g) ls[g].init(sb, m, qr.R[g]);
+        std::vector<int> stop(G, -1);  // block step at which a group met tol
+        std::vector<std::vector<cd>> hist(G);
+        int jend = m - 1;
+        for (int j = 0; j < m; ++j) {
+            // Z_j = M^{-1}_cycle V_j ; W = A Z_j
+            cplx<ZT>* Zj = Z + (long long)j * vs;
+            cycle<ZT, double>(c, 0, c->V + (long long)j * vs, Zj, s);
+            helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), opA, Zj, c->W, s);
+            c128* H1 = c->small + SL.oH1;
+            c128* H2 = c->small + SL.oH2;
+            cgs2(c, c->W, j + 1, s, sb, H1, H2);
+            CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * 2 * SL.oH2,
+                                        cudaMemcpyDeviceToHost, c->st));
+            st = sync(c);
+            if (st != HELM_OK) return st;
+            // H_{i,j} = H1 + H2 per group, and the reference norms
+            std::vector<double> ref2(s, 0.0);
+            std::vector<std::vector<cd>> hcol(G);
+            const int ld = (m + 1) * sb;
+            for (int g = 0; g < G; ++g) hcol[g].assign((size_t)ld * sb, 0.0);
+            for (int i = 0; i <= j; ++i)
+                for (int g = 0; g < G; ++g)
+                    for (int a = 0; a < sb; ++a)
+                        for (int b = 0; b < sb; ++b) {
+                            long long o = ((long long)i * G + g) * sb * sb + a * sb + b;
+                            cd h = cd(c->hsmall[SL.oH1 + o].re, c->hsmall[SL.oH1 + o].im) +
+                                   cd(c->hsmall[SL.oH2 + o].re, c->hsmall[SL.oH2 + o].im);
+                            hcol[g][(size_t)b * ld + i * sb + a] = h;
+                            if (g * sb + b < s) ref2[g * sb + b] += std::norm(h);
+                        }
+            // W = V_{j+1} H_{j+1,j}
+            st = block_qr(c, c->W, c->V + (long long)(j + 1) * vs, j + 1, s, sb, ref2, qr, dep);
+            if (st != HELM_OK) return st;
+            bool all_stop = true;
+            for (int g = 0; g < G; ++g) {
+                for (int a = 0; a < sb; ++a)
+                    for (int b = 0; b < sb; ++b)
+                        hcol[g][(size_t)b * ld + (j + 1) * sb + a] = qr.R[g][a * sb + b];
+                if (done[g] || stop[g] >= 0) continue;
+                std::vector<double> est = ls[g].add(j, hcol[g], ld);
+                iters[g] += 1;
+                bool ok = true;
+                for (int b = 0; b < sb && g * sb + b < s; ++b) ok = ok && est[b] <= tol * bn[g * sb + b];
+                if (ok) stop[g] = j;
+                else all_stop = false;
+            }
+            if (all_stop) { jend = j; break; }
+        }
+        // X += sum_j Z_j Y_j per group
+        cd* hY = reinterpret_cast<cd*>(c->hsmall + SL.oY);
+        std::memset(hY, 0, sizeof(c128) * (size_t)(jend + 1) * SL.blk);
+        for (int g = 0; g < G; ++g) {
+            if (done[g]) continue;
+            int jg = stop[g] >= 0 ? stop[g] : jend;
+            std::vector<cd> Y = ls[g].solve(jg);
+            for (int jj = 0; jj <= jg; ++jj)
+                for (int a = 0; a < sb; ++a)
+                    for (int b = 0; b < sb; ++b)
+                        hY[((size_t)jj * G + g) * sb * sb + a * sb + b] = Y[(size_t)(jj * sb + a) * sb + b];
+        }
+        CUDA_TRY(c, cudaMemcpyAsync(c->small + SL.oY, hY, sizeof(c128) * (size_t)(jend + 1) * SL.blk,
+                                    cudaMemcpyHostToDevice, c->st));
+        helm::launch_combine<ZT>(c->L(), c->X, 1.0, 1.0, Z, jend + 1, vs, c->small + SL.oY, N, s, sb);
+    }
+finish:
+    if (info) {
+        for (int j = 0; j < s; ++j) {
+            if (info->iters) info->iters[j] = iters[j / sb];
+            if (info->relres) info->relres[j] = rel[j];
+            if (info->status)
+                info->status[j] = (result == HELM_ERR_NONFINITE) ? HELM_ERR_NONFINITE
+                                  : (rel[j] <= tol ? HELM_OK : HELM_NOT_CONVERGED);
+        }
+    }
+    return result;
+}
+
+helm_status solve_internal(helm_ctx* c, const c128* Qd, int s, double tol, c128* Ud,
+                           helm_info* info, bool conjugate) {
+    if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
+    if (s < 0 || (s > 0 && (!Qd || !Ud)) || !(tol > 0.0))
+        return fail(c, HELM_ERR_ARG, "bad arguments to solve");
+    if (s == 0) return HELM_OK;
+    helm_status st = ensure_workspace(c, s);
+    if (st != HELM_OK) return st;
+    const long long N = c->N();
+    helm::launch_to_internal(c->L(), Qd, c->Bint, N, s, conjugate);
+    if (c->p.prec == HELM_PLAIN_C128)
+        st = fgmres<double>(c, s, tol, info);
+    else
+        st = fgmres<float>(c, s, tol, info);
+    if (st == HELM_ERR_ARG || st == HELM_ERR_CUDA || st == HELM_ERR_NOMEM || st == HELM_ERR_BREAKDOWN)
+        return st;
+    helm::launch_from_internal(c->L(), c->X, Ud, N, s, conjugate);
+    helm_status st2 = sync(c);
+    if (st2 != HELM_OK) return st2;
+    return st;
+}
+
+}  // namespace
+
+namespace {
+template <typename T>
+helm_status smooth_t(helm_ctx* c, int level, const void* u_in, const void* f, void* u_out,
+                            int s, int sweeps) {
+    helm_status st = ensure_workspace(c, s);
+    if (st != HELM_OK) return st;
+    const cplx<T>* cur = static_cast<const cplx<T>*>(u_in);
+    cplx<T>* tmp = reinterpret_cast<cplx<T>*>(c->lv[level].u0);
+    cplx<T>* tmp2 = reinterpret_cast<cplx<T>*>(c->lv[level].u1);
+    for (int k = 0; k < sweeps; ++k) {
+        cplx<T>* dst = (k == sweeps - 1) ? static_cast<cplx<T>*>(u_out) : (k % 2 == 0 ? tmp : tmp2);
+        smooth_level<T, T>(c, level, cur, static_cast<const cplx<T>*>(f), dst, s);
+        cur = dst;
+    }
+    return sync(c);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+
+extern "C" {
+
+void helm_default_params(helm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->h = 1.0;
+    p->shift = 0.5;
+    p->levels = 3;
+    p->pre = 2;
+    p->post = 2;
+    p->jacobi_w = 0.8;
+    p->restart = 10;
+    p->block = 8;
+    p->max_restarts = 50;
+    p->prec = HELM_PLAIN_C128;
+    p->learned_weights = nullptr;
+}
+
+helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_params* p,
+                       void* cuda_stream, helm_ctx** out) {
+    if (!out) return fail(nullptr, HELM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!m || !gamma_tilde || !p) return fail(nullptr, HELM_ERR_ARG, "null argument");
+    if (p->dim != 2 && p->dim != 3) return fail(nullptr, HELM_ERR_ARG, "dim must be 2 or 3");
+    if (p->levels < 1 || p->levels > 12 || p->pre < 0 || p->post < 0 || p->restart < 1 ||
+        p->block < 1 || p->max_restarts < 0 || !(p->h > 0) || !(p->omega >= 0))
+        return fail(nullptr, HELM_ERR_ARG, "bad parameter");
+    if (p->prec != HELM_PLAIN_C128 && p->prec != HELM_MIXED_C64 && p->prec != HELM_MIXED_C64_LEARNED)
+        return fail(nullptr, HELM_ERR_ARG, "bad precision policy");
+    int nodes[3] = {1, 1, 1};
+    for (int k = 0; k < p->dim; ++k) {
+        if (p->n[k] < 1) return fail(nullptr, HELM_ERR_ARG, "cells per axis must be >= 1");
+        if (p->n[k] % (1 << (p->levels - 1)))
+            return fail(nullptr, HELM_ERR_ARG, "cells per axis must be divisible by 2^(levels-1)");
+        nodes[k] = p->n[k] + 1;
+    }
+    helm_ctx* c = new helm_ctx();
+    c->p = *p;
+    c->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    c->inv_h2 = 1.0 / (p->h * p->h);
+    c->lv.resize(p->levels);
+    for (int l = 0; l < p->levels; ++l) {
+        Grid g;
+        g.dim = p->dim;
+        g.n1 = (nodes[0] - 1) / (1 << l) + 1;
+        g.n2 = (nodes[1] - 1) / (1 << l) + 1;
+        g.n3 = p->dim == 3 ? (nodes[2] - 1) / (1 << l) + 1 : 1;
+        g.N = (long long)g.n1 * g.n2 * g.n3;
+        c->lv[l].g = g;
+    }
+    const int K = p->dim == 3 ? 27 : 9;
+    auto cleanup = [&](helm_status s) { helm_destroy(c); return s; };
+    helm_status st;
+#define SETUP_TRY(expr)                                                                \
+    do {                                                                               \
+        cudaError_t e_ = (expr);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            st = fail(nullptr, e_ == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA, \
+                      std::string(#expr) + ": " + cudaGetErrorString(e_));             \
+            return cleanup(st);                                                        \
+        }                                                                              \
+    } while (0)
+    const long long N0 = c->lv[0].g.N;
+    double *dm = nullptr, *dg = nullptr;
+    SETUP_TRY(dalloc(&dm, sizeof(double) * N0));
+    SETUP_TRY(dalloc(&dg, sizeof(double) * N0));
+    SETUP_TRY(cudaMemcpyAsync(dm, m, sizeof(double) * N0, cudaMemcpyDefault, c->st));
+    SETUP_TRY(cudaMemcpyAsync(dg, gamma_tilde, sizeof(double) * N0, cudaMemcpyDefault, c->st));
+    SETUP_TRY(dalloc(&c->cA, sizeof(c128) * N0));
+    SETUP_TRY(dalloc(&c->cM, sizeof(c128) * N0));
+    SETUP_TRY(dalloc(&c->cA32, sizeof(c64) * N0));
+    SETUP_TRY(dalloc(&c->cM32, sizeof(c64) * N0));
+    for (int l = 0; l < p->levels; ++l) {
+        long long Nl = c->lv[l].g.N;
+        SETUP_TRY(dalloc(&c->lv[l].coef, sizeof(c128) * Nl * K));
+        SETUP_TRY(dalloc(&c->lv[l].dinv, sizeof(c128) * Nl));
+        SETUP_TRY(dalloc(&c->lv[l].coef32, sizeof(c64) * Nl * K));
+        SETUP_TRY(dalloc(&c->lv[l].dinv32, sizeof(c64) * Nl));
+    }
+    Launch L = c->L();
+    helm::launch_fine_setup(L, c->lv[0].g, dm, dg, p->omega, p->shift, c->inv_h2, c->cA, c->cM,
+                            c->lv[0].dinv, c->lv[0].coef);
+    for (int l = 1; l < p->levels; ++l) {
+        helm::launch_galerkin(L, c->lv[l - 1].g, c->lv[l].g, c->lv[l - 1].coef, c->lv[l].coef);
+        helm::launch_diag_inv(L, c->lv[l].g, c->lv[l].coef, c->lv[l].dinv);
+    }
+    helm::launch_round_c64(L, c->cA, c->cA32, N0);
+    helm::launch_round_c64(L, c->cM, c->cM32, N0);
+    for (int l = 0; l < p->levels; ++l) {
+        long long Nl = c->lv[l].g.N;
+        helm::launch_round_c64(L, c->lv[l].coef, c->lv[l].coef32, Nl * K);
+        helm::launch_round_c64(L, c->lv[l].dinv, c->lv[l].dinv32, Nl);
+    }
+    // coarsest inverse by Gauss-Jordan with partial pivoting (FP64)
+    const Grid& gcst = c->lv[p->levels - 1].g;
+    if (gcst.N > 20000) {
+        dfree(dm); dfree(dg);
+        return cleanup(fail(nullptr, HELM_ERR_ARG, "coarsest grid too large for the dense solve; add levels"));
+    }
+    c->nc = (int)gcst.N;
+    const int n = c->nc;
+    c128 *aug = nullptr, *factor = nullptr, *pivval = nullptr;
+    int *piv = nullptr, *dstatus = nullptr;
+    SETUP_TRY(dalloc(&aug, sizeof(c128) * (size_t)n * 2 * n));
+    SETUP_TRY(dalloc(&factor, sizeof(c128) * n));
+    SETUP_TRY(dalloc(&pivval, sizeof(c128)));
+    SETUP_TRY(dalloc(&piv, sizeof(int)));
+    SETUP_TRY(dalloc(&dstatus, sizeof(int)));
+    SETUP_TRY(cudaMemsetAsync(dstatus, 0, sizeof(int), c->st));
+    SETUP_TRY(dalloc(&c->Minv, sizeof(c128) * (size_t)n * n));
+    SETUP_TRY(dalloc(&c->Minv32, sizeof(c64) * (size_t)n * n));
+    // dense matrix into the left half of aug (row stride 2n): build it in Minv then copy rows
+    helm::launch_stencil_to_dense(L, gcst, c->lv[p->levels - 1].coef, c->Minv);
+    SETUP_TRY(cudaMemcpy2DAsync(aug, sizeof(c128) * 2 * n, c->Minv, sizeof(c128) * n,
+                                sizeof(c128) * n, n, cudaMemcpyDeviceToDevice, c->st));
+    helm::launch_gauss_jordan(L, aug, n, factor, piv, pivval, dstatus);
+    helm::launch_extract_inverse(L, aug, n, c->Minv, c->Minv32);
+    int hstatus = 0;
+    SETUP_TRY(cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    SETUP_TRY(cudaStreamSynchronize(c->st));
+    SETUP_TRY(cudaGetLastError());
+    dfree(aug); dfree(factor); dfree(pivval); dfree(piv); dfree(dstatus); dfree(dm); dfree(dg);
+    if (hstatus) return cleanup(fail(nullptr, HELM_ERR_BREAKDOWN, "coarsest operator is singular"));
+#undef SETUP_TRY
+    *out = c;
+    return HELM_OK;
+}
+
+helm_status helm_solve(helm_ctx* ctx, const void* Q, int s, double tol, void* U, helm_info* info) {
+    return solve_internal(ctx, static_cast<const c128*>(Q), s, tol, static_cast<c128*>(U), info,
+                          false);
+}
+
+helm_status helm_adjoint(helm_ctx* ctx, const void* B, int s, double tol, void* Lout,
+                         helm_info* info) {
+    return solve_internal(ctx, static_cast<const c128*>(B), s, tol, static_cast<c128*>(Lout), info,
+                          true);
+}
+
+helm_status helm_solve_host(helm_ctx* c, const void* Q_host, int s, double tol, void* U_host,
+                            helm_info* info) {
+    if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
+    if (s <= 0 || !Q_host || !U_host) return fail(c, HELM_ERR_ARG, "bad arguments to solve_host");
+    helm_status st = ensure_workspace(c, s);
+    if (st != HELM_OK) return st;
+    const size_t bytes = sizeof(c128) * (size_t)c->N() * s;
+    if (!c->abi_in) {
+        CUDA_TRY(c, dalloc(&c->abi_in, bytes));
+        CUDA_TRY(c, dalloc(&c->abi_out, bytes));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->abi_in, Q_host, bytes, cudaMemcpyHostToDevice, c->st));
+    helm_status r = solve_internal(c, c->abi_in, s, tol, c->abi_out, info, false);
+    if (r == HELM_ERR_ARG || r == HELM_ERR_CUDA || r == HELM_ERR_NOMEM) return r;
+    CUDA_TRY(c, cudaMemcpyAsync(U_host, c->abi_out, bytes, cudaMemcpyDeviceToHost, c->st));
+    helm_status st2 = sync(c);
+    return st2 != HELM_OK ? st2 : r;
+}
+
+helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* Q, const int* s, int nprob,
+                             double tol, void* const* U, helm_info* infos) {
+    if (nprob < 0 || (nprob > 0 && (!ctxs || !Q || !s || !U)))
+        return fail(nullptr, HELM_ERR_ARG, "bad batch arguments");
+    helm_status first = HELM_OK;
+    for (int k = 0; k < nprob; ++k) {
+        helm_status st = helm_solve(ctxs[k], Q[k], s[k], tol, U[k], infos ? &infos[k] : nullptr);
+        if (st != HELM_OK && first == HELM_OK) first = st;
+    }
+    return first;
+}
+
+void helm_destroy(helm_ctx* c) {
+    if (!c) return;
+    delete c->prof;
+    c->prof = nullptr;
+    free_workspace(c);
+    for (auto& l : c->lv) {
+        dfree(l.coef); dfree(l.dinv); dfree(l.coef32); dfree(l.dinv32);
+    }
+    dfree(c->cA); dfree(c->cM); dfree(c->cA32); dfree(c->cM32); dfree(c->Minv); dfree(c->Minv32);
+    delete c;
+}
+
+const char* helm_last_error(const helm_ctx* c) {
+    if (c) return c->err.c_str();
+    return g_thread_error.c_str();
+}
+
+helm_status helm_level_shape(const helm_ctx* c, int level, int* nodes, long long* count) {
+    if (!c || level < 0 || level >= (int)c->lv.size()) return fail(nullptr, HELM_ERR_ARG, "bad level");
+    const Grid& g = c->lv[level].g;
+    if (nodes) { nodes[0] = g.n1; nodes[1] = g.n2; nodes[2] = g.n3; }
+    if (count) *count = g.N;
+    return HELM_OK;
+}
+
+helm_status helm_apply(helm_ctx* c, int level, int op, int prec, const void* x, void* y, int s) {
+    if (!c || level < 0 || level >= (int)c->lv.size() || (op == 0 && level != 0) || op < 0 || op > 1 ||
+        prec < 0 || prec > 1 || !x || !y || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_apply");
+    Launch L = c->L();
+    if (prec == 0) {
+        auto xx = static_cast<const c128*>(x);
+        auto yy = static_cast<c128*>(y);
+        if (level == 0)
+            helm::launch_apply<double, double, double, helm::FineOp<double>>(L, fine_op<double>(c, op == 1), xx, yy, s);
+        else
+            helm::launch_apply<double, double, double, helm::GalOp<double>>(L, gal_op<double>(c, level), xx, yy, s);
+    } else {
+        auto xx = static_cast<const c64*>(x);
+        auto yy = static_cast<c64*>(y);
+        if (level == 0)
+            helm::launch_apply<float, float, float, helm::FineOp<float>>(L, fine_op<float>(c, op == 1), xx, yy, s);
+        else
+            helm::launch_apply<float, float, float, helm::GalOp<float>>(L, gal_op<float>(c, level), xx, yy, s);
+    }
+    return sync(c);
+}
+
+helm_status helm_smooth(helm_ctx* c, int level, int prec, const void* u_in, const void* f,
+                        void* u_out, int s, int sweeps) {
+    if (!c || level < 0 || level >= (int)c->lv.size() || prec < 0 || prec > 1 || !f || !u_out ||
+        s < 1 || sweeps < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_smooth");
+    return prec == 0 ? smooth_t<double>(c, level, u_in, f, u_out, s, sweeps)
+                     : smooth_t<float>(c, level, u_in, f, u_out, s, sweeps);
+}
+
+helm_status helm_restrict_residual(helm_ctx* c, int level, int prec, const void* u, const void* f,
+                                   void* rc, int s) {
+    if (!c || level < 0 || level + 1 >= (int)c->lv.size() || prec < 0 || prec > 1 || !f || !rc || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_restrict_residual");
+    if (prec == 0)
+        restrict_level<double, double>(c, level, static_cast<const c128*>(u), static_cast<const c128*>(f),
+                                       static_cast<c128*>(rc), s);
+    else
+        restrict_level<float, float>(c, level, static_cast<const c64*>(u), static_cast<const c64*>(f),
+                                     static_cast<c64*>(rc), s);
+    return sync(c);
+}
+
+helm_status helm_prolong_add(helm_ctx* c, int level, int prec, const void* ec, void* u, int s) {
+    if (!c || level < 0 || level + 1 >= (int)c->lv.size() || prec < 0 || prec > 1 || !ec || !u || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_prolong_add");
+    if (prec == 0)
+        helm::launch_prolong_add<double>(c->L(), c->lv[level].g, c->lv[level + 1].g,
+                                         static_cast<const c128*>(ec), static_cast<c128*>(u), s);
+    else
+        helm::launch_prolong_add<float>(c->L(), c->lv[level].g, c->lv[level + 1].g,
+                                        static_cast<const c64*>(ec), static_cast<c64*>(u), s);
+    return sync(c);
+}
+
+helm_status helm_coarse_solve(helm_ctx* c, int prec, const void* f, void* u, int s) {
+    if (!c || prec < 0 || prec > 1 || !f || !u || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_coarse_solve");
+    if (prec == 0) coarsest<double>(c, static_cast<const c128*>(f), static_cast<c128*>(u), s);
+    else coarsest<float>(c, static_cast<const c64*>(f), static_cast<c64*>(u), s);
+    return sync(c);
+}
+
+helm_status helm_vcycle(helm_ctx* c, int prec, const void* f, void* z, int s) {
+    if (!c || prec < 0 || prec > 1 || !f || !z || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_vcycle");
+    helm_status st = ensure_workspace(c, s);
+    if (st != HELM_OK) return st;
+    if (prec == 0) cycle<double, double>(c, 0, static_cast<const c128*>(f), static_cast<c128*>(z), s);
+    else cycle<float, double>(c, 0, static_cast<const c128*>(f), static_cast<c64*>(z), s);
+    return sync(c);
+}
+
+helm_status helm_get_operator(const helm_ctx* c, int level, void* coef_host) {
+    if (!c || level < 0 || level >= (int)c->lv.size() || !coef_host)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_get_operator");
+    const int K = c->p.dim == 3 ? 27 : 9;
+    cudaError_t e = cudaMemcpyAsync(coef_host, c->lv[level].coef, sizeof(c128) * c->lv[level].g.N * K,
+                                    cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return fail(nullptr, HELM_ERR_CUDA, cudaGetErrorString(e));
+    return HELM_OK;
+}
+
+long long helm_kernel_launches(const helm_ctx* c) { return c ? c->launches : 0; }
+
+static const char* kKernelNames[helm::KID_COUNT] = {
+    "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",
+    "restrict_fine", "restrict_coarse", "prolong_add", "coarsest_dense", "gram", "gram_reduce",
+    "combine", "layout", "random_fill", "setup"};
+
+helm_status helm_profile_enable(helm_ctx* c, int enable) {
+    if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
+    if (enable) {
+        if (!c->prof) c->prof = new helm::Profiler();
+        c->prof->reset();
+    } else {
+        delete c->prof;
+        c->prof = nullptr;
+    }
+    return HELM_OK;
+}
+
+int helm_profile_kernel_count(void) { return helm::KID_COUNT; }
+
+const char* helm_profile_kernel_name(int kid) {
+    return (kid >= 0 && kid < helm::KID_COUNT) ? kKernelNames[kid] : "";
+}
+
+helm_status helm_profile_read(helm_ctx* c, int kid, double* time_ms, long long* launches,
+                              double* bytes, double* flops) {
+    if (!c || !c->prof || kid < 0 || kid >= helm::KID_COUNT)
+        return fail(c, HELM_ERR_ARG, "profiling is off or bad kernel id");
+    c->prof->resolve();
+    if (time_ms) *time_ms = c->prof->time_ms[kid];
+    if (launches) *launches = c->prof->launches[kid];
+    if (bytes) *bytes = c->prof->bytes[kid];
+    if (flops) *flops = c->prof->flops[kid];
+    return HELM_OK;
+}
+
+}  // extern "C"

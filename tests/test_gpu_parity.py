@@ -1,0 +1,289 @@
+"""GPU path (libhelm through its C-ABI) against the FP64 CPU oracle.
+
+Every test here runs the CUDA kernels on the current device and compares
+element by element with ``oracle.helmholtz`` on the same seeded inputs.
+Tolerances: complex128 kernels 1e-12 relative (rounding order only),
+complex64 kernels 2e-5 relative (FP32 rounding of the coefficients and of
+the arithmetic), whole solves by the true FP64 residual of the oracle's own
+operator and by the error against the oracle's tight solve (<= 1e-5 at
+relative residual 1e-10).
+"""
+import numpy as np
+import pytest
+
+from oracle import helmholtz as O
+from paper_1607_00968_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1607_00968_gb300 import helm
+    helm.load()
+    return helm
+
+
+def crand(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def layered(cells, seed=0, width=4, h=25.0, ppw=10.0):
+    v = I.layered_velocity_2d(seed, cells) if len(cells) == 2 else I.layered_velocity_3d(seed, cells)
+    shape = I.node_shape(cells)
+    return 1.0 / v ** 2, I.absorbing_gamma(shape, width), h, I.omega_for_ppw(h, ppw=ppw)
+
+
+def dev(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def kpoint(Msp, shape):
+    """Oracle sparse operator -> per-node K-point stencil (K = 3^d), the
+    layout helm_get_operator returns."""
+    d = len(shape)
+    K = 3 ** d
+    N = int(np.prod(shape))
+    out = np.zeros((N, K), dtype=np.complex128)
+    Mc = Msp.tocoo()
+    ri = np.array(np.unravel_index(Mc.row, shape))
+    ci = np.array(np.unravel_index(Mc.col, shape))
+    off = ci - ri           # numpy axis order (x_d ... x_1)
+    o = np.zeros(Mc.nnz, dtype=np.int64)
+    for ax in range(d):     # numpy axis d-1 is x1 (weight 1), axis 0 is x_d
+        k = d - 1 - ax
+        o += (off[ax] + 1) * 3 ** k
+    out[Mc.row, o] = Mc.data
+    return out
+
+
+CASES_2D = [((40, 24), 3), ((24, 16), 2)]
+CASES_3D = [((16, 12, 8), 3)]
+
+
+# --------------------------------------------------------------------------
+# operators and multigrid components
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cells,levels", CASES_2D + CASES_3D)
+def test_stencil_apply(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels)
+    A = O.helmholtz_matrix(m, g, om, h)
+    M = O.helmholtz_matrix(m, g, om, h, 0.5)
+    rng = np.random.default_rng(1)
+    for s in (1, 5, 8):
+        x = crand(rng, S.N, s)
+        yA = S.apply(dev(x), 0, "A").cpu().numpy()
+        yM = S.apply(dev(x), 0, "M").cpu().numpy()
+        assert rel(yA, A @ x) < 1e-13
+        assert rel(yM, M @ x) < 1e-13
+        y32 = S.apply(dev(x, torch.complex64), 0, "A").cpu().numpy()
+        assert rel(y32, A @ x) < 2e-5
+
+
+@pytest.mark.parametrize("cells,levels", CASES_2D + CASES_3D)
+def test_galerkin_coefficients(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels)
+    Hh = O.Hierarchy(O.helmholtz_matrix(m, g, om, h, 0.5), m.shape, levels)
+    for l in range(levels):
+        ref = kpoint(Hh.M[l], Hh.shapes[l])
+        got = S.operator(l)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cells,levels", CASES_2D + CASES_3D)
+def test_coarse_level_apply_smooth_transfer(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels)
+    Hh = O.Hierarchy(O.helmholtz_matrix(m, g, om, h, 0.5), m.shape, levels)
+    rng = np.random.default_rng(2)
+    s = 3
+    for l in range(levels):
+        N = Hh.M[l].shape[0]
+        x, f = crand(rng, N, s), crand(rng, N, s)
+        assert rel(S.apply(dev(x), l, "M").cpu().numpy(), Hh.M[l] @ x) < 1e-13
+        sm = S.smooth(dev(f), dev(x), level=l, sweeps=2).cpu().numpy()
+        assert rel(sm, O.jacobi(Hh.M[l], Hh.diag[l], x, f, 0.8, 2)) < 1e-13
+        sm0 = S.smooth(dev(f), None, level=l, sweeps=1).cpu().numpy()
+        assert rel(sm0, O.jacobi(Hh.M[l], Hh.diag[l], 0 * x, f, 0.8, 1)) < 1e-13
+        sm32 = S.smooth(dev(f, torch.complex64), dev(x, torch.complex64), level=l, sweeps=2)
+        assert rel(sm32.cpu().numpy(), O.jacobi(Hh.M[l], Hh.diag[l], x, f, 0.8, 2)) < 5e-5
+        if l + 1 < levels:
+            rc = S.restrict_residual(dev(x), dev(f), level=l).cpu().numpy()
+            assert rel(rc, Hh.P[l].T @ (f - Hh.M[l] @ x)) < 1e-13
+            ec = crand(rng, Hh.M[l + 1].shape[0], s)
+            u = S.prolong_add(dev(ec), dev(x), level=l).cpu().numpy()
+            assert rel(u, x + Hh.P[l] @ ec) < 1e-14
+
+
+@pytest.mark.parametrize("cells,levels", CASES_2D + CASES_3D)
+def test_coarsest_solve_and_vcycle(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels)
+    Hh = O.Hierarchy(O.helmholtz_matrix(m, g, om, h, 0.5), m.shape, levels)
+    rng = np.random.default_rng(3)
+    fc = crand(rng, Hh.M[-1].shape[0], 4)
+    uc = S.coarse_solve(dev(fc)).cpu().numpy()
+    assert rel(uc, O.lu_solve(Hh.coarse_lu, fc)) < 1e-11
+    f = crand(rng, S.N, 6)
+    z = S.vcycle(dev(f), "c128").cpu().numpy()
+    zr = O.vcycle(Hh, f)
+    assert rel(z, zr) < 1e-11
+    z32 = S.vcycle(dev(f), "c64").cpu().numpy()
+    assert rel(z32, zr) < 1e-4
+
+
+# --------------------------------------------------------------------------
+# whole solves
+# --------------------------------------------------------------------------
+
+def oracle_solver(m, g, h, om, levels):
+    return O.Solver(m, g, om, h, levels=levels)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("cells,levels,s,block", [((64, 32), 3, 8, 8), ((64, 32), 3, 5, 2),
+                                                  ((16, 16, 8), 3, 4, 4)])
+def test_solve_matches_oracle(H, prec, cells, levels, s, block):
+    m, g, h, om = layered(cells, width=6)
+    S = H.Solver(m, g, h, om, levels=levels, block=block, restart=10, prec=prec)
+    So = oracle_solver(m, g, h, om, levels)
+    shape = m.shape
+    pos = I.line_positions(shape, s, 2, 6) if len(cells) == 2 else \
+        [(0, shape[1] // 2, 2 + 2 * k) for k in range(s)]
+    Q = I.point_sources(shape, pos, h)           # (s, N) ABI layout
+    U, info, st = S.solve(dev(Q), tol=1e-10)
+    U = U.cpu().numpy()
+    rr = O.relres(So.A, U.T, Q.T)
+    assert np.all(rr <= 1e-10), rr
+    Uo, infos = So.solve(Q.T.copy(), tol=1e-10, restart=10, block=block)
+    for k in range(s):
+        assert rel(U[k], Uo[:, k]) <= 1e-5
+    assert np.all(info.status == 0)
+    np.testing.assert_allclose(info.relres, rr, rtol=1e-6, atol=1e-13)
+    if prec == "c128":
+        # same algorithm in FP64: identical cycle counts up to rounding
+        for gi, inf in enumerate(infos):
+            got = info.iters[gi * block]
+            assert abs(int(got) - inf.iters) <= 1, (got, inf.iters)
+
+
+def test_solve_default_tolerance_full_shape_sample(H):
+    """Salt model 512 x 256, 64 sources, mixed precision, tol 1e-6: the true
+    residual of every column, computed by the oracle's own FP64 operator."""
+    P = I.salt2d_problem(seed=0, freq_hz=5.0)
+    S = H.Solver(P.m, P.gamma, P.h, P.omega, levels=4, block=8, prec="c64")
+    Q = P.rhs()
+    U, info, st = S.solve(dev(Q), tol=1e-6)
+    A = O.helmholtz_matrix(P.m, P.gamma, P.omega, P.h)
+    rr = O.relres(A, U.cpu().numpy().T, Q.T)
+    assert np.all(rr <= 1e-6), rr.max()
+
+
+def test_adjoint_and_reciprocity(H):
+    m, g, h, om = layered((64, 32), width=6)
+    S = H.Solver(m, g, h, om, levels=3, block=2)
+    A = O.helmholtz_matrix(m, g, om, h)
+    rng = np.random.default_rng(4)
+    B = crand(rng, 2, S.N)
+    L, info, _ = S.adjoint(dev(B), tol=1e-11)
+    L = L.cpu().numpy()
+    AH = A.conj().T
+    assert rel((AH @ L.T).T, B) <= 1e-10
+    a, b = 100, S.N - 300
+    E = np.zeros((2, S.N), dtype=complex)
+    E[0, a] = E[1, b] = 1.0
+    U, _, _ = S.solve(dev(E), tol=1e-11)
+    U = U.cpu().numpy()
+    assert abs(U[0, b] - U[1, a]) <= 1e-8 * abs(U[0, b])
+
+
+def test_dst_closed_form(H):
+    import scipy.fft
+    cells = (64, 32)
+    shape = I.node_shape(cells)
+    h, m0 = 1.0, 1.0
+
+    def spectrum(om):
+        lam = -om ** 2 * m0 * np.ones(shape)
+        for ax, n in enumerate(shape):
+            k = np.arange(1, n + 1)
+            v = [1, 1]
+            v[ax] = n
+            lam = lam + (4 / h ** 2 * np.sin(np.pi * k / (2 * (n + 1))) ** 2).reshape(v)
+        return lam
+
+    # indefinite, with the eigenvalue nearest zero well separated from it
+    om = max(np.linspace(0.3, 0.5, 201),
+             key=lambda w: np.min(np.abs(spectrum(w))) / np.max(np.abs(spectrum(w))))
+    lam = spectrum(om)
+    assert np.min(lam) < 0 < np.max(lam)
+    assert np.min(np.abs(lam)) >= 1e-3 * np.max(np.abs(lam))
+    rng = np.random.default_rng(5)
+    q = crand(rng, int(np.prod(shape)))
+    uh = (scipy.fft.dstn(q.real.reshape(shape), type=1, norm="ortho")
+          + 1j * scipy.fft.dstn(q.imag.reshape(shape), type=1, norm="ortho")) / lam
+    u_ref = (scipy.fft.idstn(uh.real, type=1, norm="ortho")
+             + 1j * scipy.fft.idstn(uh.imag, type=1, norm="ortho")).ravel()
+    S = H.Solver(np.full(shape, m0), np.zeros(shape), h, om, levels=3, block=1, max_restarts=200)
+    U, info, _ = S.solve(dev(q[None]), tol=1e-11)
+    assert rel(U.cpu().numpy()[0], u_ref) <= 1e-8
+
+
+def test_edge_cases(H):
+    m, g, h, om = layered((32, 16), width=4)
+    S = H.Solver(m, g, h, om, levels=2, block=4)
+    A = O.helmholtz_matrix(m, g, om, h)
+    rng = np.random.default_rng(6)
+    q = crand(rng, S.N)
+    Q = np.stack([q, np.zeros_like(q), q, 2j * q])
+    U, info, st = S.solve(dev(Q), tol=1e-10)
+    U = U.cpu().numpy()
+    assert np.all(U[1] == 0)
+    assert info.relres[1] == 0
+    assert rel(U[2], U[0]) <= 1e-8 and rel(U[3], 2j * U[0]) <= 1e-8
+    assert np.all(O.relres(A, U.T, Q.T) <= 1e-10)
+    # all-zero block
+    U0, info0, st0 = S.solve(dev(np.zeros((3, S.N), dtype=complex)), tol=1e-6)
+    assert st0 == 0 and torch.count_nonzero(U0).item() == 0
+    # single column, one-level hierarchy without shift: the preconditioner is
+    # the exact inverse, so one block step converges
+    S1 = H.Solver(m, g, h, om, levels=1, block=1, shift=0.0)
+    U1, info1, _ = S1.solve(dev(q[None]), tol=1e-12)
+    assert rel(U1.cpu().numpy()[0], O.dense_solve(A, q)) <= 1e-9
+    assert info1.iters[0] == 1
+
+
+def test_bad_arguments_raise(H):
+    m, g, h, om = layered((32, 16))
+    with pytest.raises(H.HelmError):
+        H.Solver(m, g, h, om, levels=6)       # 16 cells not divisible by 2^5
+    S = H.Solver(m, g, h, om, levels=2)
+    with pytest.raises(H.HelmError):
+        S.solve(dev(np.ones((1, S.N), dtype=complex)), tol=-1.0)
+
+
+def test_not_converged_returns_best_iterate(H):
+    m, g, h, om = layered((64, 32), width=6)
+    S = H.Solver(m, g, h, om, levels=3, block=2, restart=2, max_restarts=1)
+    Q = I.point_sources(m.shape, I.line_positions(m.shape, 2, 2, 6), h)
+    U, info, st = S.solve(dev(Q), tol=1e-12, check=False)
+    assert st == H.HELM_NOT_CONVERGED
+    A = O.helmholtz_matrix(m, g, om, h)
+    rr = O.relres(A, U.cpu().numpy().T, Q.T)
+    np.testing.assert_allclose(info.relres, rr, rtol=1e-6)
+    assert np.all(rr < 1.0)
