@@ -190,6 +190,27 @@ helm_status helm_coarse_solve(helm_ctx* ctx, int prec, const void* f, void* u,
    (prec 0) or complex64 (prec 1). */
 helm_status helm_vcycle(helm_ctx* ctx, int prec, const void* f, void* z, int s);
 
+/* helm_vcycle without any allocation.  It exists for callers that cannot
+   call cudaMalloc at solve time: code running while a CUDA stream is being
+   captured into a graph, latency-bound loops that cannot afford the device
+   synchronisation an allocation may cause, or frameworks whose allocator
+   owns all device memory.  It computes what helm_vcycle computes (same
+   kernels, same arguments and layouts), but its level buffers live in one
+   fixed 64 MiB device array compiled into libhelm instead of context
+   workspace; every GPU that loads libhelm holds that array until the process
+   exits.  The level buffers need 16 (prec 0) or 8 (prec 1) bytes per node
+   per column, twice on the fine grid and four times on each coarser grid
+   (each rounded up to 256 bytes); a call needing more than 64 MiB returns
+   HELM_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree
+   or other allocating routine.  The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress) with that device current;
+   make that first call before any stream capture.  All calls share the
+   array and it keeps the last call's contents; calls that overlap on the
+   GPU (other streams, other threads on the same device) race, and the
+   context must not be used by another thread during the call.  The paper
+   has no counterpart of this entry point. */
+helm_status helm_vcycle_noalloc(helm_ctx* ctx, int prec, const void* f, void* z, int s);
+
 /* Copy the FP64 stencil of M_level to host: count x K complex128 values,
    K = 9 (2D) or 27 (3D), offset o = sum_k (d_k+1) 3^k for d_k in {-1,0,1}
    along axis k (x1 first); zero where the neighbour is outside the grid.

@@ -14,6 +14,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -1091,6 +1092,97 @@ helm_status helm_get_operator(const helm_ctx* c, int level, void* coef_host) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) return fail(nullptr, HELM_ERR_CUDA, cudaGetErrorString(e));
     return HELM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// helm_vcycle_noalloc: the V-cycle with its level buffers in a fixed device
+// array instead of context workspace.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(64) << 20;   // 64 MiB
+constexpr int kMaxDevices = 64;
+
+// Level buffers of helm_vcycle_noalloc.  Every GPU that loads libhelm holds
+// this array until the process exits.  Host code must not use its name as an
+// address: the device address comes from cudaGetSymbolAddress below.
+__device__ __align__(256) unsigned char g_vcycle_scratch[kNoAllocBytes];
+
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+// Device address of g_vcycle_scratch on the current device, looked up once
+// per device (with that device current) and cached.
+helm_status scratch_address(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, HELM_ERR_CUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, HELM_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_vcycle_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(nullptr, HELM_ERR_CUDA,
+                        std::string("cudaGetSymbolAddress(g_vcycle_scratch): ") + cudaGetErrorString(e));
+        g_scratch_addr[dev] = ptr;
+    }
+    *out = g_scratch_addr[dev];
+    return HELM_OK;
+}
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, int s) {
+    if (!c || prec < 0 || prec > 1 || !f || !z || s < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_vcycle_noalloc");
+    const size_t esz = prec == 0 ? sizeof(c128) : sizeof(c64);
+    // level 0 needs two buffers (u0, u1); every coarser level four (u0, u1, e, f)
+    size_t need = 0;
+    for (size_t l = 0; l < c->lv.size(); ++l)
+        need += (l == 0 ? 2 : 4) * round256(esz * (size_t)c->lv[l].g.N * (size_t)s);
+    if (need > kNoAllocBytes)
+        return fail(c, HELM_ERR_ARG,
+                    "helm_vcycle_noalloc: " + std::to_string(need) + " bytes of level buffers needed, "
+                    "the fixed scratch holds " + std::to_string(kNoAllocBytes) +
+                    "; use fewer columns or helm_vcycle");
+    void* base = nullptr;
+    helm_status st = scratch_address(&base);
+    if (st != HELM_OK) return fail(c, st, helm_last_error(nullptr));
+    // Point the context's level buffers into the scratch for this call, then
+    // put the context's own buffers back.  Nothing needs zeroing: every level
+    // buffer is written in full before it is read (the cycle zero-fills its
+    // correction buffer itself when there is no pre-smoothing).
+    void* saved[12][4];  // helm_setup allows at most 12 levels
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        saved[l][0] = c->lv[l].u0; saved[l][1] = c->lv[l].u1;
+        saved[l][2] = c->lv[l].e;  saved[l][3] = c->lv[l].f;
+    }
+    unsigned char* p = static_cast<unsigned char*>(base);
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        size_t b = round256(esz * (size_t)c->lv[l].g.N * (size_t)s);
+        c->lv[l].u0 = p; p += b;
+        c->lv[l].u1 = p; p += b;
+        if (l > 0) {
+            c->lv[l].e = p; p += b;
+            c->lv[l].f = p; p += b;
+        }
+    }
+    if (prec == 0) cycle<double, double>(c, 0, static_cast<const c128*>(f), static_cast<c128*>(z), s);
+    else cycle<float, double>(c, 0, static_cast<const c128*>(f), static_cast<c64*>(z), s);
+    st = sync(c);
+    for (size_t l = 0; l < c->lv.size(); ++l) {
+        c->lv[l].u0 = saved[l][0]; c->lv[l].u1 = saved[l][1];
+        c->lv[l].e = saved[l][2];  c->lv[l].f = saved[l][3];
+    }
+    return st;
 }
 
 long long helm_kernel_launches(const helm_ctx* c) { return c ? c->launches : 0; }

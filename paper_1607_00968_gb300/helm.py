@@ -27,7 +27,7 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_apply", "helm_smooth", "helm_restrict_residual", "helm_prolong_add",
            "helm_coarse_solve", "helm_vcycle", "helm_get_operator", "helm_kernel_launches",
            "helm_profile_enable", "helm_profile_kernel_count", "helm_profile_kernel_name",
-           "helm_profile_read"]
+           "helm_profile_read", "helm_vcycle_noalloc"]
 
 
 class HelmParams(ctypes.Structure):
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_prolong_add": (i, [vp, i, i, vp, vp, i]),
         "helm_coarse_solve": (i, [vp, i, vp, vp, i]),
         "helm_vcycle": (i, [vp, i, vp, vp, i]),
+        "helm_vcycle_noalloc": (i, [vp, i, vp, vp, i]),
         "helm_get_operator": (i, [vp, i, vp]),
         "helm_kernel_launches": (ll, [vp]),
         "helm_profile_enable": (i, [vp, i]),
