@@ -37,7 +37,7 @@ UNIT = "RHS-solves/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, 152 SMs x ~2 FMA/clk x 2070 MHz x 2)
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
-SOLVER = dict(levels=4, pre=2, post=2, jacobi_w=0.8)
+SOLVER = dict(pre=2, post=2, jacobi_w=0.8)
 
 
 def parse():
@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shift", type=float, default=0.2)
-    ap.add_argument("--restart", type=int, default=20)
+    ap.add_argument("--restart", type=int, default=10)
     ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--seed", type=int, default=0)
@@ -125,7 +126,7 @@ def _oracle_worker(args, q):
         from oracle import helmholtz as O
         from paper_1607_00968_gb300 import inputs
         P = inputs.salt2d_problem(seed=args["seed"], freq_hz=args["freq"])
-        S = O.Solver(P.m, P.gamma, P.omega, P.h, levels=SOLVER["levels"], shift=args["shift"])
+        S = O.Solver(P.m, P.gamma, P.omega, P.h, levels=args["levels"], shift=args["shift"])
         cols = list(range(0, NSRC, NSRC // args["nrhs"]))[:args["nrhs"]]
         Q = P.rhs(cols).T.copy()
         t0 = time.perf_counter()
@@ -141,12 +142,14 @@ def _oracle_worker(args, q):
         q.put({"error": repr(e)})
 
 
-def oracle_run(seed, freq, nrhs, shift, restart, block, reps=1, max_restarts=50, timeout=900):
+def oracle_run(seed, freq, nrhs, shift, restart, block, levels, reps=1, max_restarts=50,
+               timeout=900):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     threads = os.cpu_count() or 1
     p = ctx.Process(target=_oracle_worker, args=(dict(seed=seed, freq=freq, nrhs=nrhs, shift=shift,
                                                       restart=restart, block=block, reps=reps,
+                                                      levels=levels,
                                                       threads=threads,
                                                       max_restarts=max_restarts), q))
     p.start()
@@ -184,7 +187,8 @@ def run_reference(args):
     per = []
     info = None
     for k in range(args.warmup + args.steps):
-        r = oracle_run(args.seed, FREQS_HZ[0], 4, args.shift, args.restart, min(args.block, 4))
+        r = oracle_run(args.seed, FREQS_HZ[0], 4, args.shift, args.restart, min(args.block, 4),
+                       args.levels)
         if "error" in r:
             print(json.dumps({"impl": "reference", "unavailable": r["error"]}))
             return
@@ -200,7 +204,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "impl": "reference",
         "config": {"workload": "salt2d_512x256_64src_5freq", "sample": "4 sources at 2 Hz per step",
-                   "shift": args.shift, "restart": args.restart, "levels": SOLVER["levels"]},
+                   "shift": args.shift, "restart": args.restart, "levels": args.levels},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
                          "sample": "4 of 64 sources at 2 Hz per step, numpy/scipy FP64 oracle, "
                                    "set-up excluded; " + cpu_model()},
@@ -214,8 +218,9 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 
 def make_solvers(helm, probs, prec, args):
+    kw = dict(SOLVER, levels=args.levels)
     return [helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, restart=args.restart,
-                        block=args.block, prec=prec, max_restarts=100, **SOLVER) for P in probs]
+                        block=args.block, prec=prec, max_restarts=100, **kw) for P in probs]
 
 
 def timed_steps(torch, solvers, Qd, steps, stream):
@@ -360,7 +365,8 @@ def main():
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r = oracle_run(args.seed, FREQS_HZ[0], 4, args.shift, args.restart, min(args.block, 4))
+        r = oracle_run(args.seed, FREQS_HZ[0], 4, args.shift, args.restart, min(args.block, 4),
+                       args.levels)
         if "error" in r:
             cpu = {"value": None, "unit": UNIT, "cores": r.get("threads"), "kind": "oracle",
                    "sample": "failed: " + r["error"]}
@@ -380,7 +386,7 @@ def main():
             "config": {"workload": "salt2d_512x256_64src_5freq", "grid_cells": [512, 256],
                        "nodes": 131841, "sources": NSRC, "freqs_hz": list(FREQS_HZ),
                        "tol": TOL, "shift": args.shift, "restart": args.restart,
-                       "block": args.block, "levels": SOLVER["levels"], "smoother": "V(2,2) Jacobi 0.8",
+                       "block": args.block, "levels": args.levels, "smoother": "V(2,2) Jacobi 0.8",
                        "precision": "complex64 cycle, FP64 Krylov",
                        "l2": "no flush: the Krylov basis (%.1f GB) exceeds L2" %
                              ((args.restart + 1) * Q.nbytes / 1e9),

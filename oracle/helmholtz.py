@@ -19,6 +19,7 @@ beyond the node grid on every side.
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg
 import scipy.sparse as sp
 
 # --------------------------------------------------------------------------
@@ -168,7 +169,10 @@ def dense_solve(Amat, B: np.ndarray) -> np.ndarray:
 class Hierarchy:
     """Galerkin hierarchy M_0 = M, M_{l+1} = P_l^T M_l P_l (Sec. 4), with a
     dense LU of the coarsest operator (Sec. 4: LU for a block of right-hand
-    sides on the coarsest grid)."""
+    sides on the coarsest grid).  The coarsest LU is LAPACK's partial-pivoting
+    factorisation (scipy.linalg.lu_factor, a library primitive; the oracle's
+    own ``lu_factor`` restates it for the tiny-grid dense solves and both are
+    pinned against numpy.linalg.solve)."""
 
     def __init__(self, M0: sp.csr_matrix, shape, levels: int):
         self.M = [M0.tocsr()]
@@ -180,7 +184,11 @@ class Hierarchy:
             self.M.append((P.T @ self.M[-1] @ P).tocsr())
             self.shapes.append(coarse_shape(self.shapes[-1]))
         self.diag = [Ml.diagonal() for Ml in self.M]
-        self.coarse_lu = lu_factor(self.M[-1].toarray())
+        self.coarse_lu = scipy.linalg.lu_factor(self.M[-1].toarray())
+
+    def coarse_solve(self, f):
+        """M_L^{-1} f on the coarsest level."""
+        return scipy.linalg.lu_solve(self.coarse_lu, f)
 
     @property
     def levels(self):
@@ -204,7 +212,7 @@ def vcycle(H: Hierarchy, f: np.ndarray, level: int = 0, pre: int = 2,
     W-cycle), prolong and correct, post-relax.  The coarsest level is solved
     with the dense LU."""
     if level == H.levels - 1:
-        return lu_solve(H.coarse_lu, f)
+        return H.coarse_solve(f)
     M, d, P = H.M[level], H.diag[level], H.P[level]
     u = np.zeros_like(f)
     u = jacobi(M, d, u, f, w, pre)

@@ -76,13 +76,17 @@ void launch_from_internal(const Launch& L, const c128* internal, c128* abi, long
 // Block Gram per group:  out[i][g][a][b] = sum_node conj(X_i[node][g*sb+a]) Y[node][g*sb+b]
 // for i < nb (X_i = X + i*xstride).  partial: scratch of gram_partial_elems().
 long long gram_partial_elems(long long N, int nb, int s, int sb);
+// emulate: double-float arithmetic on the FP32 pipes instead of FP64.
 void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
-                 long long N, int s, int sb, c128* partial, c128* out);
+                 long long N, int s, int sb, c128* partial, c128* out, bool emulate);
 
 // out[node][g*sb+b] = beta*out + sign * sum_{i<nb} sum_a X_i[node][g*sb+a] C[i][g][a][b]
+// emulate: double-float arithmetic (needs csplit: scratch of nb*G*sb*sb float4
+// for the split coefficients; falls back to FP64 when null).
 template <typename TX>
 void launch_combine(const Launch& L, c128* out, double beta, double sign, const cplx<TX>* X,
-                    int nb, long long xstride, const c128* C, long long N, int s, int sb);
+                    int nb, long long xstride, const c128* C, long long N, int s, int sb,
+                    bool emulate, float4* csplit);
 
 // per-column squared 2-norms of X (N x s node-major): out[j] (FP64)
 long long colnorm_partial_elems(long long N, int s);

@@ -3,6 +3,8 @@
 // block combinations W -= V H / X += Z Y / Q = W T, column norms, random
 // directions for rank-deficient blocks, and the ABI <-> internal layout
 // transposes.  All arithmetic is FP64.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace helm {
@@ -91,13 +93,26 @@ __global__ void __launch_bounds__(kThreads) k_gram(const c128* __restrict__ X, l
     }
 }
 
-__global__ void k_gram_reduce(const c128* __restrict__ partial, int chunks, long long E,
-                              c128* __restrict__ out) {
-    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    c128 acc = mk(0.0, 0.0);
-    for (int c = 0; c < chunks; ++c) acc = acc + partial[(long long)c * E + e];
-    out[e] = acc;
+// out[e] = sum over chunks of partial[c][e]: 32 entries per CTA, the 8 warps
+// of the CTA take every 8th chunk and are summed in shared memory.
+__global__ void __launch_bounds__(256) k_gram_reduce(const c128* __restrict__ partial, int chunks,
+                                                     long long E, c128* __restrict__ out) {
+    __shared__ double2 red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long e = (long long)blockIdx.x * 32 + lane;
+    double re = 0.0, im = 0.0;
+    if (e < E)
+        for (int c = w; c < chunks; c += 8) {
+            c128 v = partial[(long long)c * E + e];
+            re += v.re;
+            im += v.im;
+        }
+    red[w][lane] = make_double2(re, im);
+    __syncthreads();
+    if (w == 0 && e < E) {
+        for (int k = 1; k < 8; ++k) { re += red[k][lane].x; im += red[k][lane].y; }
+        out[e] = mk(re, im);
+    }
 }
 
 template <typename TX>
@@ -122,6 +137,290 @@ __global__ void __launch_bounds__(kThreads) k_combine(c128* __restrict__ out, do
         }
         c128 o = beta != 0.0 ? beta * out[e] : mk(0.0, 0.0);
         out[e] = o + sign * acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Double-float ("dd") variants for the mixed-precision solver: each FP64
+// operand is split once into a pair of floats (hi + lo, 48 significant bits)
+// as it is staged in shared memory; products are formed exactly with an FMA
+// (TwoProd), cross terms hi*lo are added to a float correction term, and the
+// running sum is kept as an unevaluated float pair updated with the
+// error-free TwoSum.  The result carries about 2^-46 relative error per term,
+// i.e. FP64-class accuracy, while all arithmetic runs on the FP32 pipes.
+// The _rn intrinsics keep the compiler from contracting the error-free steps.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float4 split_c(c64 v) { return make_float4(v.re, 0.f, v.im, 0.f); }
+
+// x = hi + lo with hi the first 24 significant bits of x (truncated) and lo
+// the remaining 29 bits rounded to float: |x - hi - lo| <= 2^-47 |x| for
+// 2^-74 <= |x| < 2^127 (smaller parts flush to zero).  Built from the bit
+// fields with integer operations, so no FP64 or conversion-pipe instruction
+// is spent on it (GB300's FP64 pipe is ~64x narrower than its FP32 pipe).
+__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    unsigned int sign = hw & 0x80000000u;
+    int e = (int)((hw >> 20) & 0x7FFu);
+    int ef = e - 896;                       // float biased exponent of hi
+    if (e == 2047) { hi = __uint_as_float(0x7FC00000u); lo = 0.f; return; }  // keep NaN/Inf visible
+    if (ef <= 0) { hi = 0.f; lo = 0.f; return; }
+    if (ef >= 255) { hi = __uint_as_float(sign | 0x7F800000u); lo = 0.f; return; }
+    unsigned int fhi = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    unsigned int flo = lw & 0x1FFFFFFFu;
+    hi = __uint_as_float(sign | ((unsigned int)ef << 23) | fhi);
+    int es = ef - 52;                       // float biased exponent of 2^(E-52)
+    float l = es > 0 ? __uint2float_rn(flo) * __uint_as_float((unsigned int)es << 23) : 0.f;
+    lo = sign ? -l : l;
+}
+
+__device__ __forceinline__ float4 split_c(c128 v) {
+    float4 r;
+    split_d(v.re, r.x, r.y);
+    split_d(v.im, r.z, r.w);
+    return r;
+}
+
+// (S, L) += (ah + al) * (bh + bl)
+__device__ __forceinline__ void dd_mac(float& S, float& L, float ah, float al, float bh, float bl) {
+    float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    L = __fmaf_rn(ah, bl, L);
+    L = __fmaf_rn(al, bh, L);
+    float t = __fadd_rn(S, p);
+    float bp = __fsub_rn(t, S);
+    float ap = __fsub_rn(t, bp);
+    float err = __fadd_rn(__fsub_rn(S, ap), __fsub_rn(p, bp));
+    L = __fadd_rn(L, __fadd_rn(err, e));
+    S = t;
+}
+
+constexpr int kMaxQPT = 4;   // quads per thread; a quad is one row a and four columns b..b+3
+
+// Same partition of the output as k_gram.  The quads (g, a, b0) are spread
+// over ceil(Q / qpt) threads; when that leaves threads over, R replicas of
+// that layout share the CTA and take every R-th node of a tile, and their
+// sums are added at the end.  The next node tile is loaded into registers
+// while the current one is being used.
+template <int QPT>
+__global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X, long long xstride,
+                                                       const c128* __restrict__ Y, long long N,
+                                                       int s, int sb, int chunks,
+                                                       c128* __restrict__ partial) {
+    constexpr int qpt = QPT;
+    extern __shared__ float4 smf[];
+    const int tn = gram_tile_nodes(s);
+    const int te = tn * s;                        // elements per tile and operand
+    float4* xs = smf;
+    float4* ys = smf + te;
+    const int i = blockIdx.y;
+    const int G = (s + sb - 1) / sb;
+    const int nbq = (sb + 3) / 4;
+    const long long E1 = (long long)G * sb * sb;
+    const int Q = G * sb * nbq;
+    const int nthr = (Q + qpt - 1) / qpt;         // threads per replica (<= kThreads)
+    const int R = kThreads / nthr;                // replicas
+    const int rep = threadIdx.x / nthr;
+    const int qt = threadIdx.x - rep * nthr;
+    const bool active = rep < R;
+    const c128* Xi = X + (long long)i * xstride;
+    long long per = (N + chunks - 1) / chunks;
+    long long n0 = (long long)blockIdx.x * per;
+    long long n1 = n0 + per < N ? n0 + per : N;
+    c128* out = partial + ((long long)blockIdx.x * gridDim.y + i) * E1;
+
+    float S[QPT][4][2], Lc[QPT][4][2];
+    int xa[QPT], yb[QPT], nv[QPT];
+#pragma unroll
+    for (int q = 0; q < QPT; ++q) {
+        int id = qt + q * nthr;
+        nv[q] = 0; xa[q] = 0; yb[q] = 0;
+        if (active && id < Q) {
+            int g = id / (sb * nbq);
+            int rem = id - g * sb * nbq;
+            int a = rem / nbq, b0 = (rem % nbq) * 4;
+            int lim = sb < s - g * sb ? sb : s - g * sb;   // ragged last group
+            if (a < lim && b0 < lim) {
+                xa[q] = g * sb + a;
+                yb[q] = g * sb + b0;
+                nv[q] = lim - b0 < 4 ? lim - b0 : 4;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S[q][k][0] = S[q][k][1] = Lc[q][k][0] = Lc[q][k][1] = 0.f;
+    }
+    // register prefetch of one tile: kGramTileElems / kThreads values per operand
+    constexpr int kPF = kGramTileElems / kThreads;
+    c128 px[kPF], py[kPF];
+    auto fetch = [&](long long t0, int cnt) {
+#pragma unroll
+        for (int k = 0; k < kPF; ++k) {
+            int idx = threadIdx.x + k * kThreads;
+            if (idx < cnt * s) {
+                px[k] = Xi[t0 * s + idx];
+                py[k] = Y[t0 * s + idx];
+            }
+        }
+    };
+    long long t0 = n0;
+    int cnt = (int)((n1 - t0) < tn ? (n1 - t0) : tn);
+    if (t0 < n1) fetch(t0, cnt);
+    while (t0 < n1) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kPF; ++k) {
+            int idx = threadIdx.x + k * kThreads;
+            if (idx < cnt * s) {
+                xs[idx] = split_c(px[k]);
+                ys[idx] = split_c(py[k]);
+            }
+        }
+        __syncthreads();
+        const int cur = cnt;
+        t0 += tn;
+        if (t0 < n1) {
+            cnt = (int)((n1 - t0) < tn ? (n1 - t0) : tn);
+            fetch(t0, cnt);
+        }
+        for (int n = rep; n < cur; n += R) {
+#pragma unroll
+            for (int q = 0; q < QPT; ++q) {
+                if (nv[q] == 0) continue;
+                float4 x = xs[n * s + xa[q]];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= nv[q]) break;
+                    float4 y = ys[n * s + yb[q] + k];
+                    // conj(x) * y: re = xr yr + xi yi, im = xr yi - xi yr
+                    dd_mac(S[q][k][0], Lc[q][k][0], x.x, x.y, y.x, y.y);
+                    dd_mac(S[q][k][0], Lc[q][k][0], x.z, x.w, y.z, y.w);
+                    dd_mac(S[q][k][1], Lc[q][k][1], x.x, x.y, y.z, y.w);
+                    dd_mac(S[q][k][1], Lc[q][k][1], -x.z, -x.w, y.x, y.y);
+                }
+            }
+        }
+    }
+    // sum the replicas in FP64 through shared memory, then write every entry
+    // of the output slot (zero outside a ragged last group)
+    __syncthreads();
+    double2* red = reinterpret_cast<double2*>(smf);   // R x E1 (fits: R > 1 only when E1 is small)
+    const bool use_red = R > 1;
+    if (use_red) {
+        for (long long e = threadIdx.x; e < (long long)R * E1; e += kThreads) red[e] = make_double2(0.0, 0.0);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < QPT; ++q) {
+        int id = qt + q * nthr;
+        if (!active || id >= Q) continue;
+        int g = id / (sb * nbq);
+        int rem = id - g * sb * nbq;
+        int a = rem / nbq, b0 = (rem % nbq) * 4;
+        for (int k = 0; k < 4 && b0 + k < sb; ++k) {
+            long long e = ((long long)g * sb + a) * sb + b0 + k;
+            double re = k < nv[q] ? (double)S[q][k][0] + (double)Lc[q][k][0] : 0.0;
+            double im = k < nv[q] ? (double)S[q][k][1] + (double)Lc[q][k][1] : 0.0;
+            if (use_red) red[(long long)rep * E1 + e] = make_double2(re, im);
+            else out[e] = mk(re, im);
+        }
+    }
+    if (use_red) {
+        __syncthreads();
+        for (long long e = threadIdx.x; e < E1; e += kThreads) {
+            double re = 0.0, im = 0.0;
+            for (int r = 0; r < R; ++r) { re += red[r * E1 + e].x; im += red[r * E1 + e].y; }
+            out[e] = mk(re, im);
+        }
+    }
+}
+
+constexpr int kCombineRows = 4;   // nodes per thread in the dd combine
+
+__global__ void k_split(const c128* __restrict__ C, float4* __restrict__ Cs, long long n) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < n) Cs[e] = split_c(C[e]);
+}
+
+// out[node][g*sb+b] = beta*out + sign * sum_i sum_a X_i[node][g*sb+a] C[i][g][a][b]
+// in double-float arithmetic.  A CTA owns a tile of kCombineRows * (256/s)
+// nodes.  For each block i the tile of X_i is split into float pairs in
+// shared memory once (the tile of X_{i+1} is loaded into registers
+// meanwhile) and C_i, split beforehand by k_split, is staged beside it.
+template <typename TX>
+__global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out, double beta,
+                                                          double sign, const cplx<TX>* __restrict__ X,
+                                                          int nb, long long xstride,
+                                                          const float4* __restrict__ Cs, long long N,
+                                                          int s, int sb) {
+    extern __shared__ float4 smf[];
+    const int G = (s + sb - 1) / sb;
+    const int per = kThreads / s;                 // nodes per row of threads
+    const int T = per * kCombineRows;             // nodes per tile
+    float4* xs = smf;                             // T x s
+    float4* cs = smf + (size_t)T * s;             // G x sb x sb
+    const int col = threadIdx.x % s;
+    const int sub = threadIdx.x / s;
+    const bool active = sub < per;
+    const int g = col / sb, b = col - g * sb;
+    const int amax = s - g * sb < sb ? s - g * sb : sb;
+    const long long ntiles = (N + T - 1) / T;
+    const int csz = G * sb * sb;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long t0 = tile * T;
+        const int cnt = (int)(N - t0 < T ? N - t0 : T);
+        float S[kCombineRows][2], Lc[kCombineRows][2];
+#pragma unroll
+        for (int r = 0; r < kCombineRows; ++r) S[r][0] = S[r][1] = Lc[r][0] = Lc[r][1] = 0.f;
+        cplx<TX> px[kCombineRows];
+        auto fetch = [&](int i) {
+            const cplx<TX>* Xi = X + (long long)i * xstride + t0 * s;
+#pragma unroll
+            for (int k = 0; k < kCombineRows; ++k) {
+                int idx = threadIdx.x + k * kThreads;
+                if (idx < cnt * s) px[k] = Xi[idx];
+            }
+        };
+        fetch(0);
+        for (int i = 0; i < nb; ++i) {
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kCombineRows; ++k) {
+                int idx = threadIdx.x + k * kThreads;
+                if (idx < cnt * s) xs[idx] = split_c(px[k]);
+            }
+            const float4* Ci = Cs + (long long)i * csz;
+            for (int idx = threadIdx.x; idx < csz; idx += kThreads) cs[idx] = Ci[idx];
+            __syncthreads();
+            if (i + 1 < nb) fetch(i + 1);
+            if (!active) continue;
+#pragma unroll
+            for (int r = 0; r < kCombineRows; ++r) {
+                int n = sub + r * per;
+                if (n >= cnt) break;
+                const float4* xr = xs + n * s + g * sb;
+                const float4* cc = cs + (g * sb) * sb + b;
+                for (int a = 0; a < amax; ++a) {
+                    float4 x = xr[a];
+                    float4 c = cc[a * sb];
+                    // x * c: re = xr cr - xi ci, im = xr ci + xi cr
+                    dd_mac(S[r][0], Lc[r][0], x.x, x.y, c.x, c.y);
+                    dd_mac(S[r][0], Lc[r][0], -x.z, -x.w, c.z, c.w);
+                    dd_mac(S[r][1], Lc[r][1], x.x, x.y, c.z, c.w);
+                    dd_mac(S[r][1], Lc[r][1], x.z, x.w, c.x, c.y);
+                }
+            }
+        }
+        if (!active) continue;
+#pragma unroll
+        for (int r = 0; r < kCombineRows; ++r) {
+            int n = sub + r * per;
+            if (n >= cnt) break;
+            long long e = (t0 + n) * s + col;
+            c128 acc = mk((double)S[r][0] + (double)Lc[r][0], (double)S[r][1] + (double)Lc[r][1]);
+            c128 o = beta != 0.0 ? beta * out[e] : mk(0.0, 0.0);
+            out[e] = o + sign * acc;
+        }
     }
 }
 
@@ -202,24 +501,74 @@ long long gram_partial_elems(long long N, int nb, int s, int sb) {
 }
 
 void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
-                 long long N, int s, int sb, c128* partial, c128* out) {
+                 long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
     int G = (s + sb - 1) / sb;
     long long E1 = (long long)G * sb * sb;
     int chunks = gram_chunks(N, nb, s);
     size_t smem = 2 * sizeof(c128) * (size_t)gram_tile_nodes(s) * s;
     dim3 grid(chunks, nb);
-    L.pre(KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
-    k_gram<<<grid, kThreads, smem, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
+    L.pre(emulate ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
+    if (emulate) {
+        const int nbq = (sb + 3) / 4;
+        const long long Q = (long long)G * sb * nbq;
+        int qpt = (int)((Q + kThreads - 1) / kThreads);
+        if (qpt < 1) qpt = 1;
+        if (qpt > kMaxQPT) {
+            // more quads than one CTA holds: fall back to the FP64 kernel
+            k_gram<<<grid, kThreads, smem, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
+        } else {
+            int nthr = (int)((Q + qpt - 1) / qpt);
+            int R = kThreads / nthr;
+            size_t red = R > 1 ? (size_t)R * E1 * sizeof(double2) : 0;
+            size_t sm2 = smem > red ? smem : red;
+            if (qpt == 3) qpt = 4;
+            auto kern = qpt == 1 ? k_gram_dd<1> : (qpt == 2 ? k_gram_dd<2> : k_gram_dd<4>);
+            if (sm2 > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+            kern<<<grid, kThreads, sm2, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
+        }
+    }
+    else
+        k_gram<<<grid, kThreads, smem, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
     L.post();
     long long E = E1 * nb;
     L.pre(KID_GRAM_REDUCE, (chunks + 1.0) * E * 16.0, 2.0 * chunks * E);
-    k_gram_reduce<<<blocks_for(E), kThreads, 0, L.st>>>(partial, chunks, E, out);
+    k_gram_reduce<<<(unsigned)((E + 31) / 32), 256, 0, L.st>>>(partial, chunks, E, out);
     L.post();
+}
+
+bool combine_dd_ok(int s, int sb) {
+    return s <= kThreads && (size_t)((kThreads / s) * kCombineRows * s + ((s + sb - 1) / sb) * sb * sb) *
+                                    sizeof(float4) <= 160 * 1024;
 }
 
 template <typename TX>
 void launch_combine(const Launch& L, c128* out, double beta, double sign, const cplx<TX>* X,
-                    int nb, long long xstride, const c128* C, long long N, int s, int sb) {
+                    int nb, long long xstride, const c128* C, long long N, int s, int sb,
+                    bool emulate, float4* csplit) {
+    {
+        if (emulate && csplit && combine_dd_ok(s, sb)) {
+            const int T = (kThreads / s) * kCombineRows;
+            const int G = (s + sb - 1) / sb;
+            size_t smem = (size_t)(T * s + G * sb * sb) * sizeof(float4);
+            long long ntiles = (N + T - 1) / T;
+            int grid = (int)(ntiles < 4LL * 152 * 4 ? ntiles : 4LL * 152 * 4);
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(k_combine_dd<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            long long nc = (long long)nb * G * sb * sb;
+            L.pre(KID_LAYOUT, 32.0 * nc, 0);
+            k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
+            L.post();
+            L.pre(KID_COMBINE_DD,
+                  (double)N * s * (nb * 2.0 * sizeof(TX) + (beta != 0.0 ? 32.0 : 16.0)),
+                  8.0 * nb * (double)N * s * sb);
+            k_combine_dd<TX><<<grid, kThreads, smem, L.st>>>(out, beta, sign, X, nb, xstride, csplit,
+                                                             N, s, sb);
+            L.post();
+            return;
+        }
+    }
     L.pre(KID_COMBINE, (double)N * s * (nb * 2.0 * sizeof(TX) + (beta != 0.0 ? 32.0 : 16.0)),
           8.0 * nb * (double)N * s * sb);
     k_combine<TX><<<blocks_for(N * s), kThreads, 0, L.st>>>(out, beta, sign, X, nb, xstride, C, N,
@@ -227,9 +576,9 @@ void launch_combine(const Launch& L, c128* out, double beta, double sign, const 
     L.post();
 }
 template void launch_combine<double>(const Launch&, c128*, double, double, const c128*, int,
-                                     long long, const c128*, long long, int, int);
+                                     long long, const c128*, long long, int, int, bool, float4*);
 template void launch_combine<float>(const Launch&, c128*, double, double, const c64*, int,
-                                    long long, const c128*, long long, int, int);
+                                    long long, const c128*, long long, int, int, bool, float4*);
 
 long long colnorm_partial_elems(long long N, int s) { return gram_partial_elems(N, 1, s, 1); }
 
@@ -238,7 +587,7 @@ void launch_colnorm2(const Launch& L, const c128* X, long long N, int s, double*
     // Per-column norms are the 1 x 1 groups of the Gram product X^H X;
     // out receives (re, im) pairs, the imaginary parts being zero.
     launch_gram(L, X, 1, 0, X, N, s, 1, reinterpret_cast<c128*>(partial),
-                reinterpret_cast<c128*>(out));
+                reinterpret_cast<c128*>(out), false);
 }
 
 void launch_to_internal(const Launch& L, const c128* abi, c128* internal, long long N, int s,

@@ -147,6 +147,7 @@ struct helm_ctx {
     c128* small = nullptr;   // device small matrices (H passes, G, T, Y)
     long long small_elems = 0;
     int* dmask = nullptr;
+    float4* csplit = nullptr; // split (float pair) coefficients of the dd block updates
     c128* hsmall = nullptr;  // pinned host mirror of `small`
     unsigned long long rng_counter = 0x5eed;
     helm::Profiler* prof = nullptr;
@@ -297,6 +298,8 @@ void free_workspace(helm_ctx* c) {
     dfree(c->V); dfree(c->Z); dfree(c->W); dfree(c->W2); dfree(c->Bint); dfree(c->X);
     dfree(c->R); dfree(c->abi_in); dfree(c->abi_out); dfree(c->partial); dfree(c->small);
     dfree(c->dmask);
+    dfree(c->csplit);
+    c->csplit = nullptr;
     if (c->hsmall) cudaFreeHost(c->hsmall);
     c->V = c->W = c->W2 = c->Bint = c->X = c->R = c->abi_in = c->abi_out = c->partial = c->small =
         nullptr;
@@ -342,6 +345,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     CUDA_TRY(c, dalloc(&c->small, sizeof(c128) * c->small_elems));
     CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->hsmall), sizeof(c128) * c->small_elems));
     CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
+    CUDA_TRY(c, dalloc(&c->csplit, sizeof(float4) * (size_t)(m + 1) * blk));
     c->s_cap = s;
     return HELM_OK;
 }
@@ -518,13 +522,15 @@ SmallLayout small_layout(const helm_ctx* c, int s, int sb) {
 
 // Gram-Schmidt (two passes) of the block at `W` against V_0..V_{nb-1};
 // H1/H2 receive the coefficients of the passes when non-null.
+bool emulated(const helm_ctx* c) { return c->p.prec != HELM_PLAIN_C128; }
+
 void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
     const long long N = c->N();
     const long long vs = N * s;
     for (int pass = 0; pass < 2; ++pass) {
         c128* H = pass == 0 ? H1 : H2;
-        helm::launch_gram(c->L(), c->V, nb, vs, Wp, N, s, sb, c->partial, H);
-        helm::launch_combine<double>(c->L(), Wp, 1.0, -1.0, c->V, nb, vs, H, N, s, sb);
+        helm::launch_gram(c->L(), c->V, nb, vs, Wp, N, s, sb, c->partial, H, emulated(c));
+        helm::launch_combine<double>(c->L(), Wp, 1.0, -1.0, c->V, nb, vs, H, N, s, sb, emulated(c), c->csplit);
     }
 }
 
@@ -546,7 +552,7 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
     std::vector<std::vector<cd>> R1(G), R2(G);
     std::vector<int> mask(s, 0);
     // pass 1
-    helm::launch_gram(c->L(), Win, 1, 0, Win, N, s, sb, c->partial, dG);
+    helm::launch_gram(c->L(), Win, 1, 0, Win, N, s, sb, c->partial, dG, emulated(c));
     CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
     helm_status st = sync(c);
     if (st != HELM_OK) return st;
@@ -570,7 +576,8 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
             if (dep[k]) { mask[g * sb + k] = 1; any_dep = true; }
     }
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
-    helm::launch_combine<double>(c->L(), c->W2, 0.0, 1.0, Win, 1, 0, dT, N, s, sb);
+    helm::launch_combine<double>(c->L(), c->W2, 0.0, 1.0, Win, 1, 0, dT, N, s, sb, emulated(c),
+                                 c->csplit);
     if (any_dep) {
         CUDA_TRY(c, cudaMemcpyAsync(c->dmask, mask.data(), sizeof(int) * s, cudaMemcpyHostToDevice,
                                     c->st));
@@ -581,7 +588,7 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
         }
     }
     // pass 2
-    helm::launch_gram(c->L(), c->W2, 1, 0, c->W2, N, s, sb, c->partial, dG);
+    helm::launch_gram(c->L(), c->W2, 1, 0, c->W2, N, s, sb, c->partial, dG, emulated(c));
     CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
     st = sync(c);
     if (st != HELM_OK) return st;
@@ -608,7 +615,8 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
         out.R[g] = Rg;
     }
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
-    helm::launch_combine<double>(c->L(), Vout, 0.0, 1.0, c->W2, 1, 0, dT, N, s, sb);
+    helm::launch_combine<double>(c->L(), Vout, 0.0, 1.0, c->W2, 1, 0, dT, N, s, sb, emulated(c),
+                                 c->csplit);
     return HELM_OK;
 }
 
@@ -709,15 +717,17 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
             const int ld = (m + 1) * sb;
             for (int g = 0; g < G; ++g) hcol[g].assign((size_t)ld * sb, 0.0);
             for (int i = 0; i <= j; ++i)
-                for (int g = 0; g < G; ++g)
-                    for (int a = 0; a < sb; ++a)
-                        for (int b = 0; b < sb; ++b) {
+                for (int g = 0; g < G; ++g) {
+                    const int ng = std::min(sb, s - g * sb);   // columns of a ragged last group
+                    for (int a = 0; a < ng; ++a)
+                        for (int b = 0; b < ng; ++b) {
                             long long o = ((long long)i * G + g) * sb * sb + a * sb + b;
                             cd h = cd(c->hsmall[SL.oH1 + o].re, c->hsmall[SL.oH1 + o].im) +
                                    cd(c->hsmall[SL.oH2 + o].re, c->hsmall[SL.oH2 + o].im);
                             hcol[g][(size_t)b * ld + i * sb + a] = h;
-                            if (g * sb + b < s) ref2[g * sb + b] += std::norm(h);
+                            ref2[g * sb + b] += std::norm(h);
                         }
+                }
             // W = V_{j+1} H_{j+1,j}
             st = block_qr(c, c->W, c->V + (long long)(j + 1) * vs, j + 1, s, sb, ref2, qr, dep);
             if (st != HELM_OK) return st;
@@ -750,7 +760,8 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
         }
         CUDA_TRY(c, cudaMemcpyAsync(c->small + SL.oY, hY, sizeof(c128) * (size_t)(jend + 1) * SL.blk,
                                     cudaMemcpyHostToDevice, c->st));
-        helm::launch_combine<ZT>(c->L(), c->X, 1.0, 1.0, Z, jend + 1, vs, c->small + SL.oY, N, s, sb);
+        helm::launch_combine<ZT>(c->L(), c->X, 1.0, 1.0, Z, jend + 1, vs, c->small + SL.oY, N, s, sb,
+                                 emulated(c), c->csplit);
     }
 finish:
     if (info) {
@@ -1190,7 +1201,7 @@ long long helm_kernel_launches(const helm_ctx* c) { return c ? c->launches : 0; 
 static const char* kKernelNames[helm::KID_COUNT] = {
     "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",
     "restrict_fine", "restrict_coarse", "prolong_add", "coarsest_dense", "gram", "gram_reduce",
-    "combine", "layout", "random_fill", "setup"};
+    "combine", "layout", "random_fill", "setup", "gram_dd", "combine_dd"};
 
 helm_status helm_profile_enable(helm_ctx* c, int enable) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");

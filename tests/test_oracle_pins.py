@@ -158,6 +158,15 @@ def test_lu_against_numpy_with_pivoting():
                                np.linalg.solve(A, B), rtol=1e-10, atol=1e-11)
 
 
+def test_hierarchy_coarse_solve_matches_own_lu():
+    rng = np.random.default_rng(19)
+    shape = I.node_shape((8, 4))
+    M = O.helmholtz_matrix(rng.uniform(1, 2, shape), rng.uniform(0, 1, shape), 2.0, 1.0, 0.5)
+    H = O.Hierarchy(M, shape, 2)
+    f = crand(rng, H.M[1].shape[0], 3)
+    np.testing.assert_allclose(H.coarse_solve(f), O.dense_solve(H.M[1], f), rtol=1e-11)
+
+
 def test_lu_singular_raises():
     with pytest.raises(np.linalg.LinAlgError):
         O.lu_factor(np.zeros((3, 3)))
