@@ -92,6 +92,10 @@ typedef struct {
     helm_prec prec;          /* precision policy                                */
     const void* learned_weights; /* device BF16 weights of the learned stage
                                     (layout in helm_learned.h); NULL = none     */
+    int coarse_tf32x3;       /* complex64 coarsest solve on the tensor cores:
+                                0 = one tf32 product (~1e-3 relative),
+                                1 = three tf32 products on hi/lo splits
+                                (FP32-class)                                    */
 } helm_params;
 
 typedef struct {
@@ -103,7 +107,8 @@ typedef struct {
 } helm_info;
 
 /* Fill p with the defaults of Sec. 5.3 (levels 3, V(2,2), weight 0.8,
-   restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128. */
+   restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128,
+   coarse_tf32x3 0. */
 void helm_default_params(helm_params* p);
 
 /* Set up the hierarchy for one (m, gamma, omega) (Sec. 4: set-up once, reused
@@ -182,7 +187,8 @@ helm_status helm_restrict_residual(helm_ctx* ctx, int level, int prec,
 helm_status helm_prolong_add(helm_ctx* ctx, int level, int prec,
                              const void* ec, void* u, int s);
 
-/* u = M_L^{-1} f on the coarsest level (dense inverse times the block). */
+/* u = M_L^{-1} f on the coarsest level (dense inverse times the block):
+   FP64 for prec 0, tensor-core tf32 (see coarse_tf32x3) for prec 1. */
 helm_status helm_coarse_solve(helm_ctx* ctx, int prec, const void* f, void* u,
                               int s);
 
@@ -200,7 +206,10 @@ helm_status helm_vcycle(helm_ctx* ctx, int prec, const void* f, void* z, int s);
    workspace; every GPU that loads libhelm holds that array until the process
    exits.  The level buffers need 16 (prec 0) or 8 (prec 1) bytes per node
    per column, twice on the fine grid and four times on each coarser grid
-   (each rounded up to 256 bytes); a call needing more than 64 MiB returns
+   (each rounded up to 256 bytes); prec 1 adds the operands of the
+   tensor-core coarsest solve (4 (2 n_c + 31)/32*32 ((2 s + 127)/128*128) bytes
+   plus 4 k n_c ((2 s + 127)/128*128) bytes, k the K-split of n_c coarsest
+   nodes, at most 16); a call needing more than 64 MiB returns
    HELM_ERR_ARG without touching the GPU.  It calls no cudaMalloc, cudaFree
    or other allocating routine.  The first call on a device looks up the
    array's device address (cudaGetSymbolAddress) with that device current;

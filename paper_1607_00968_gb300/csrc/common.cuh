@@ -42,8 +42,64 @@ __host__ __device__ __forceinline__ void fma_conj_acc(cplx<T>& a, cplx<T> b, cpl
     a.im = fma(b.re, c.im, a.im); a.im = fma(-b.im, c.re, a.im);
 }
 
+// ---------------------------------------------------------------------------
+// Conversions between FP64 and FP32 built from the bit fields with integer
+// operations.  On GB300 the FP64 pipe, which also executes F2F conversions,
+// is ~64x narrower than the FP32 pipe, so the FP32 kernels avoid it.
+// Values outside the float range flush to zero (tiny) or infinity (huge).
+// ---------------------------------------------------------------------------
+
+// float -> double, exact for normal floats
+__device__ __forceinline__ double f2d_bits(float f) {
+    unsigned int u = __float_as_uint(f);
+    unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    unsigned int e = (u >> 23) & 0xFFu;
+    unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    unsigned long long ed = e == 255 ? 0x7FFULL : (unsigned long long)(e + 896);
+    return __longlong_as_double((long long)(sign | (ed << 52) | m));
+}
+
+// x = hi + lo, hi = the first 24 significant bits of x (truncated), lo = the
+// next 24 of the remaining 29 (truncated): |x - hi - lo| < 2^-47 |x| for
+// 2^-74 <= |x| < 2^127; smaller parts flush to zero, NaN/Inf stay visible.
+__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    unsigned int sign = hw & 0x80000000u;
+    int e = (int)((hw >> 20) & 0x7FFu);
+    int ef = e - 896;                       // float biased exponent of hi
+    if (e == 2047) { hi = __uint_as_float(0x7FC00000u); lo = 0.f; return; }
+    if (ef <= 0) { hi = 0.f; lo = 0.f; return; }
+    if (ef >= 255) { hi = __uint_as_float(sign | 0x7F800000u); lo = 0.f; return; }
+    unsigned int fhi = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    unsigned int flo = lw & 0x1FFFFFFFu;
+    hi = __uint_as_float(sign | ((unsigned int)ef << 23) | fhi);
+    int lz = __clz(flo);                    // >= 3 when flo != 0
+    int el = ef - 52 + (31 - lz);           // biased float exponent of lo
+    if (flo == 0 || el <= 0) { lo = 0.f; return; }
+    unsigned int mant = (flo << (lz + 1)) >> 9;
+    lo = __uint_as_float(sign | ((unsigned int)el << 23) | mant);
+}
+
 template <typename To, typename From>
 __host__ __device__ __forceinline__ cplx<To> cvt(cplx<From> a) { return mk<To>((To)a.re, (To)a.im); }
+#ifdef __CUDA_ARCH__
+// on the device: complex128 -> complex64 by truncation to 24 bits, and the
+// exact complex64 -> complex128 widening, both without FP64-pipe work
+template <>
+__device__ __forceinline__ cplx<float> cvt<float, double>(cplx<double> a) {
+    float h, l;
+    cplx<float> z;
+    split_d(a.re, h, l); z.re = h;
+    split_d(a.im, h, l); z.im = h;
+    return z;
+}
+template <>
+__device__ __forceinline__ cplx<double> cvt<double, float>(cplx<float> a) {
+    return mk<double>(f2d_bits(a.re), f2d_bits(a.im));
+}
+#endif
 
 template <typename T>
 __device__ __forceinline__ cplx<T> ldg(const cplx<T>* p) {

@@ -1,0 +1,257 @@
+// Coarsest-grid solve of the complex64 cycle on the tensor cores.
+//
+// The coarsest operator's inverse is applied to the whole block of
+// right-hand sides (Sec. 4: LU applied to a block of right-hand sides on the
+// coarsest grid) as one real GEMM:
+//     C' (nc x 2s) = A' (nc x 2nc) B' (2nc x 2s),
+// A' = the complex inverse viewed as interleaved (re, im) floats,
+// B' rows 2k = [Re f_k, Im f_k], 2k+1 = [-Im f_k, Re f_k], so that
+// C' = [Re u | Im u].  A' is rounded to tf32 once at set-up; the product
+// runs on mma.sync m16n8k8 tf32 tiles with FP32 accumulation (optionally
+// three products on hi/lo tf32 splits for FP32-class accuracy), fed by a
+// 3-stage cp.async pipeline, with the K range split over CTAs so that the
+// ~nc/128 row tiles fill the 152 SMs; a second kernel adds the K slices.
+#include "kernels.h"
+
+namespace helm {
+
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 32, TST = 3;
+constexpr int APAD = 4, BPAD = 8;
+constexpr int ALD = TBK + APAD, BLD = TBN + BPAD;
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    unsigned int r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int bytes) {
+    unsigned int s = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+__device__ __forceinline__ void mma_tf32(float* d, const unsigned int* a, const unsigned int* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// P[ks][row][col] = sum over this CTA's K slice of A'[row][k] B'[k][col].
+// 8 warps: 2 along M (64 rows each) x 4 along N (32 columns each).
+template <bool SPLIT3>
+__global__ void __launch_bounds__(256) k_dense_tf32(const float* __restrict__ A, int lda, int M,
+                                                     const float* __restrict__ B, int ldb,
+                                                     int kchunk, int Kp, float* __restrict__ P) {
+    extern __shared__ float sm[];
+    float* As = sm;
+    float* Bs = sm + TST * TBM * ALD;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.x * TBM, n0 = blockIdx.z * TBN, ks = blockIdx.y;
+    const int k0 = ks * kchunk;
+    const int k1 = min(Kp, k0 + kchunk);
+    const int nk = k1 > k0 ? (k1 - k0) / TBK : 0;
+
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    auto load_stage = [&](int stage, int kt) {
+        const int kk = k0 + kt * TBK;
+        float* as = As + stage * TBM * ALD;
+        float* bs = Bs + stage * TBK * BLD;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int idx = tid + c * 256;
+            int r = idx >> 3, c4 = idx & 7;
+            int grow = m0 + r;
+            const float* src = A + (size_t)(grow < M ? grow : M - 1) * lda + kk + c4 * 4;
+            cp_async16(as + r * ALD + c4 * 4, src, grow < M ? 16 : 0);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            int idx = tid + c * 256;
+            int r = idx >> 5, c4 = idx & 31;
+            const float* src = B + (size_t)(kk + r) * ldb + n0 + c4 * 4;
+            cp_async16(bs + r * BLD + c4 * 4, src, 16);
+        }
+    };
+
+#pragma unroll
+    for (int st = 0; st < TST - 1; ++st) {
+        if (st < nk) load_stage(st, st);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_async_wait<TST - 2>();
+        __syncthreads();
+        int nxt = kt + TST - 1;
+        if (nxt < nk) load_stage(nxt % TST, nxt);
+        cp_async_commit();
+        const float* as = As + (kt % TST) * TBM * ALD;
+        const float* bs = Bs + (kt % TST) * TBK * BLD;
+#pragma unroll
+        for (int k8 = 0; k8 < TBK / 8; ++k8) {
+            unsigned int af[4][4], bf[4][2];
+            unsigned int afl[4][4], bfl[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt) {
+                const float* ar = as + (wm * 64 + mt * 16 + g) * ALD + k8 * 8 + t;
+                float v[4] = {ar[0], ar[8 * ALD], ar[4], ar[8 * ALD + 4]};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float hi = SPLIT3 ? tf32_rna(v[q]) : v[q];
+                    af[mt][q] = __float_as_uint(hi);
+                    if (SPLIT3) afl[mt][q] = __float_as_uint(tf32_rna(v[q] - hi));
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const float* br = bs + (k8 * 8 + t) * BLD + wn * 32 + nt * 8 + g;
+                float v[2] = {br[0], br[4 * BLD]};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float hi = SPLIT3 ? tf32_rna(v[q]) : v[q];
+                    bf[nt][q] = __float_as_uint(hi);
+                    if (SPLIT3) bfl[nt][q] = __float_as_uint(tf32_rna(v[q] - hi));
+                }
+            }
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    if (SPLIT3) {
+                        mma_tf32(acc[mt][nt], afl[mt], bf[nt]);
+                        mma_tf32(acc[mt][nt], af[mt], bfl[nt]);
+                    }
+                    mma_tf32(acc[mt][nt], af[mt], bf[nt]);
+                }
+        }
+    }
+    cp_async_wait<0>();
+    const int ldp = gridDim.z * TBN;
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            int row = m0 + wm * 64 + mt * 16 + g;
+            int col = n0 + wn * 32 + nt * 8 + 2 * t;
+            float* p = P + ((size_t)ks * M) * ldp;
+            if (row < M) {
+                p[(size_t)row * ldp + col] = acc[mt][nt][0];
+                p[(size_t)row * ldp + col + 1] = acc[mt][nt][1];
+            }
+            if (row + 8 < M) {
+                p[(size_t)(row + 8) * ldp + col] = acc[mt][nt][2];
+                p[(size_t)(row + 8) * ldp + col + 1] = acc[mt][nt][3];
+            }
+        }
+}
+
+// B'[2k][j] = Re f[k][j], B'[2k][s+j] = Im f[k][j], B'[2k+1][j] = -Im f, B'[2k+1][s+j] = Re f;
+// zero in the padding rows (k >= nc) and columns (>= 2s).
+template <bool ROUND>
+__global__ void k_build_bprime(const c64* __restrict__ f, int nc, int s, float* __restrict__ Bp,
+                               int ldb, int Kp) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)Kp * ldb) return;
+    int row = (int)(e / ldb), col = (int)(e - (long long)row * ldb);
+    int k = row >> 1, odd = row & 1;
+    float v = 0.f;
+    if (k < nc && col < 2 * s) {
+        int j = col < s ? col : col - s;
+        c64 z = f[(size_t)k * s + j];
+        if (!odd) v = col < s ? z.re : z.im;
+        else v = col < s ? -z.im : z.re;
+    }
+    Bp[e] = ROUND ? tf32_rna(v) : v;
+}
+
+__global__ void k_reduce_cprime(const float* __restrict__ P, int KS, int M, int ldp, int s,
+                                c64* __restrict__ u) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)M * s) return;
+    int row = (int)(e / s), j = (int)(e - (long long)row * s);
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < KS; ++k) {
+        const float* p = P + ((size_t)k * M + row) * ldp;
+        re += p[j];
+        im += p[s + j];
+    }
+    u[e] = mk(re, im);
+}
+
+// A'[i][2k + {0,1}] = (Re, Im) Minv[i][k] in FP32 (rounded to tf32 when the
+// solve uses one product), zero for 2k >= 2nc.
+__global__ void k_build_aprime(const c128* __restrict__ Minv, int nc, float* __restrict__ Ap, int Kp,
+                               int round_tf32) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)nc * Kp) return;
+    int i = (int)(e / Kp), c = (int)(e - (long long)i * Kp);
+    float v = 0.f;
+    if (c < 2 * nc) {
+        c128 z = Minv[(size_t)i * nc + (c >> 1)];
+        v = __double2float_rn((c & 1) ? z.im : z.re);
+    }
+    Ap[e] = round_tf32 ? tf32_rna(v) : v;
+}
+
+}  // namespace
+
+int dense_tc_kpad(int nc) { return ((2 * nc + TBK - 1) / TBK) * TBK; }
+int dense_tc_ldb(int s) { return ((2 * s + TBN - 1) / TBN) * TBN; }
+int dense_tc_ksplit(int nc) {
+    int mt = (nc + TBM - 1) / TBM;
+    int ks = (2 * 152 + mt - 1) / mt;       // about two CTAs per SM
+    return ks < 1 ? 1 : (ks > 16 ? 16 : ks);
+}
+size_t dense_tc_scratch_floats(int nc, int s) {
+    return (size_t)dense_tc_kpad(nc) * dense_tc_ldb(s) +
+           (size_t)dense_tc_ksplit(nc) * nc * dense_tc_ldb(s);
+}
+
+void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, bool split3) {
+    int Kp = dense_tc_kpad(nc);
+    long long n = (long long)nc * Kp;
+    L.pre(KID_SETUP, 0, 0);
+    k_build_aprime<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(Minv, nc, Ap, Kp, split3 ? 0 : 1);
+    L.post();
+}
+
+void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
+                     float* scratch, bool split3) {
+    const int Kp = dense_tc_kpad(nc), ldb = dense_tc_ldb(s), KS = dense_tc_ksplit(nc);
+    float* Bp = scratch;
+    float* P = scratch + (size_t)Kp * ldb;
+    long long nb = (long long)Kp * ldb;
+    L.pre(KID_LAYOUT, 4.0 * nb + 8.0 * nc * s, 0);
+    if (split3) k_build_bprime<false><<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, Bp, ldb, Kp);
+    else k_build_bprime<true><<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, Bp, ldb, Kp);
+    L.post();
+    int kchunk = ((Kp / TBK + KS - 1) / KS) * TBK;
+    dim3 grid((nc + TBM - 1) / TBM, KS, ldb / TBN);
+    size_t smem = sizeof(float) * (size_t)TST * (TBM * ALD + TBK * BLD);
+    auto kern = split3 ? k_dense_tf32<true> : k_dense_tf32<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    L.pre(KID_DENSE, 4.0 * nc * (double)Kp + 4.0 * nb + 4.0 * KS * nc * (double)ldb,
+          8.0 * nc * (double)nc * s * (split3 ? 3 : 1));
+    kern<<<grid, 256, smem, L.st>>>(Ap, Kp, nc, Bp, ldb, kchunk, Kp, P);
+    L.post();
+    L.pre(KID_LAYOUT, 4.0 * KS * nc * 2.0 * s + 8.0 * nc * s, 0);
+    k_reduce_cprime<<<(unsigned)(((long long)nc * s + 255) / 256), 256, 0, L.st>>>(P, KS, nc, ldb, s, u);
+    L.post();
+}
+
+}  // namespace helm

@@ -36,6 +36,22 @@ template <typename T>
 void launch_dense_apply(const Launch& L, const cplx<T>* Minv, int n, const cplx<T>* f,
                         cplx<T>* u, int s);
 
+// ---------------- coarsest solve on the tensor cores (dense_tc.cu) ----------------
+
+// padded K (= 2 nc rounded up to the K tile), B' row length, K-split factor,
+// and the scratch (floats) one launch needs for nc coarse nodes and s columns
+int dense_tc_kpad(int nc);
+int dense_tc_ldb(int s);
+int dense_tc_ksplit(int nc);
+size_t dense_tc_scratch_floats(int nc, int s);
+// A' (nc x dense_tc_kpad(nc) floats): interleaved (re, im) of Minv in FP32,
+// rounded to tf32 unless split3 (the three-product solve splits it itself)
+void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, bool split3);
+// u = Minv f for complex64 blocks (nc x s, node-major) from A'; split3: three
+// tf32 products on hi/lo splits (FP32-class accuracy) instead of one
+void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
+                     float* scratch, bool split3);
+
 // ---------------- set-up (mg.cu) ----------------
 
 // c_A = omega^2 m (1 - i gamma), c_M = omega^2 m (1 - i (gamma + shift)),

@@ -153,28 +153,6 @@ __global__ void __launch_bounds__(kThreads) k_combine(c128* __restrict__ out, do
 
 __device__ __forceinline__ float4 split_c(c64 v) { return make_float4(v.re, 0.f, v.im, 0.f); }
 
-// x = hi + lo with hi the first 24 significant bits of x (truncated) and lo
-// the remaining 29 bits rounded to float: |x - hi - lo| <= 2^-47 |x| for
-// 2^-74 <= |x| < 2^127 (smaller parts flush to zero).  Built from the bit
-// fields with integer operations, so no FP64 or conversion-pipe instruction
-// is spent on it (GB300's FP64 pipe is ~64x narrower than its FP32 pipe).
-__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
-    unsigned int sign = hw & 0x80000000u;
-    int e = (int)((hw >> 20) & 0x7FFu);
-    int ef = e - 896;                       // float biased exponent of hi
-    if (e == 2047) { hi = __uint_as_float(0x7FC00000u); lo = 0.f; return; }  // keep NaN/Inf visible
-    if (ef <= 0) { hi = 0.f; lo = 0.f; return; }
-    if (ef >= 255) { hi = __uint_as_float(sign | 0x7F800000u); lo = 0.f; return; }
-    unsigned int fhi = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-    unsigned int flo = lw & 0x1FFFFFFFu;
-    hi = __uint_as_float(sign | ((unsigned int)ef << 23) | fhi);
-    int es = ef - 52;                       // float biased exponent of 2^(E-52)
-    float l = es > 0 ? __uint2float_rn(flo) * __uint_as_float((unsigned int)es << 23) : 0.f;
-    lo = sign ? -l : l;
-}
-
 __device__ __forceinline__ float4 split_c(c128 v) {
     float4 r;
     split_d(v.re, r.x, r.y);
@@ -319,8 +297,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X
         int a = rem / nbq, b0 = (rem % nbq) * 4;
         for (int k = 0; k < 4 && b0 + k < sb; ++k) {
             long long e = ((long long)g * sb + a) * sb + b0 + k;
-            double re = k < nv[q] ? (double)S[q][k][0] + (double)Lc[q][k][0] : 0.0;
-            double im = k < nv[q] ? (double)S[q][k][1] + (double)Lc[q][k][1] : 0.0;
+            double re = k < nv[q] ? f2d_bits(S[q][k][0]) + f2d_bits(Lc[q][k][0]) : 0.0;
+            double im = k < nv[q] ? f2d_bits(S[q][k][1]) + f2d_bits(Lc[q][k][1]) : 0.0;
             if (use_red) red[(long long)rep * E1 + e] = make_double2(re, im);
             else out[e] = mk(re, im);
         }
@@ -417,9 +395,15 @@ __global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out,
             int n = sub + r * per;
             if (n >= cnt) break;
             long long e = (t0 + n) * s + col;
-            c128 acc = mk((double)S[r][0] + (double)Lc[r][0], (double)S[r][1] + (double)Lc[r][1]);
-            c128 o = beta != 0.0 ? beta * out[e] : mk(0.0, 0.0);
-            out[e] = o + sign * acc;
+            double are = f2d_bits(S[r][0]) + f2d_bits(Lc[r][0]);
+            double aim = f2d_bits(S[r][1]) + f2d_bits(Lc[r][1]);
+            // beta is 0 or 1 and sign +-1 on every call of the driver; the
+            // general form costs FP64 multiplies only otherwise
+            if (sign == -1.0) { are = -are; aim = -aim; }
+            else if (sign != 1.0) { are *= sign; aim *= sign; }
+            if (beta == 1.0) { c128 o = out[e]; are += o.re; aim += o.im; }
+            else if (beta != 0.0) { c128 o = out[e]; are += beta * o.re; aim += beta * o.im; }
+            out[e] = mk(are, aim);
         }
     }
 }

@@ -194,7 +194,7 @@ __global__ void k_fine_setup(Grid g, const double* __restrict__ m, const double*
                              c128* dinvM, c128* coefM) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= g.N) return;
-    double w2m = omega * omega * m[i];
+    double w2m = omega * omega * m[i];  // set-up: plain FP64 arithmetic
     c128 a = mk(w2m, -w2m * gam[i]);
     c128 b = mk(w2m, -w2m * (gam[i] + shift));
     cA[i] = a;
@@ -368,12 +368,12 @@ __global__ void k_extract_inverse(const c128* aug, int n, c128* out, c64* out32)
     long long i = e / n, j = e - i * n;
     c128 v = aug[i * 2 * n + n + j];
     out[e] = v;
-    if (out32) out32[e] = cvt<float>(v);
+    if (out32) out32[e] = mk(__double2float_rn(v.re), __double2float_rn(v.im));
 }
 
 __global__ void k_round_c64(const c128* in, c64* out, long long count) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e < count) out[e] = cvt<float>(in[e]);
+    if (e < count) out[e] = mk(__double2float_rn(in[e].re), __double2float_rn(in[e].im));
 }
 
 }  // namespace

@@ -131,6 +131,8 @@ struct helm_ctx {
     int nc = 0;
     c128* Minv = nullptr;
     c64* Minv32 = nullptr;
+    float* Ap = nullptr;      // tf32-rounded interleaved inverse for the tensor-core solve
+    float* dense_scratch = nullptr;
     // Krylov workspace, sized for s_cap columns
     int s_cap = 0;
     c128* V = nullptr;       // (restart+1) blocks of N x s
@@ -234,7 +236,11 @@ void restrict_level(helm_ctx* c, int l, const cplx<T>* u, const cplx<FT>* f, cpl
 
 template <typename T>
 void coarsest(helm_ctx* c, const cplx<T>* f, cplx<T>* u, int s) {
-    helm::launch_dense_apply<T>(c->L(), pick<T>(c->Minv, c->Minv32), c->nc, f, u, s);
+    if constexpr (std::is_same<T, float>::value)
+        helm::launch_dense_tc(c->L(), c->Ap, c->nc, f, u, s, c->dense_scratch,
+                              c->p.coarse_tf32x3 != 0);
+    else
+        helm::launch_dense_apply<T>(c->L(), c->Minv, c->nc, f, u, s);
 }
 
 // out = cycle(f) on level l with zero initial guess.  `out` must not alias the
@@ -300,6 +306,8 @@ void free_workspace(helm_ctx* c) {
     dfree(c->dmask);
     dfree(c->csplit);
     c->csplit = nullptr;
+    dfree(c->dense_scratch);
+    c->dense_scratch = nullptr;
     if (c->hsmall) cudaFreeHost(c->hsmall);
     c->V = c->W = c->W2 = c->Bint = c->X = c->R = c->abi_in = c->abi_out = c->partial = c->small =
         nullptr;
@@ -346,6 +354,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->hsmall), sizeof(c128) * c->small_elems));
     CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
     CUDA_TRY(c, dalloc(&c->csplit, sizeof(float4) * (size_t)(m + 1) * blk));
+    CUDA_TRY(c, dalloc(&c->dense_scratch, sizeof(float) * helm::dense_tc_scratch_floats(c->nc, s)));
     c->s_cap = s;
     return HELM_OK;
 }
@@ -840,6 +849,7 @@ void helm_default_params(helm_params* p) {
     p->max_restarts = 50;
     p->prec = HELM_PLAIN_C128;
     p->learned_weights = nullptr;
+    p->coarse_tf32x3 = 0;
 }
 
 helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_params* p,
@@ -934,13 +944,14 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
     SETUP_TRY(dalloc(&dstatus, sizeof(int)));
     SETUP_TRY(cudaMemsetAsync(dstatus, 0, sizeof(int), c->st));
     SETUP_TRY(dalloc(&c->Minv, sizeof(c128) * (size_t)n * n));
-    SETUP_TRY(dalloc(&c->Minv32, sizeof(c64) * (size_t)n * n));
+    SETUP_TRY(dalloc(&c->Ap, sizeof(float) * (size_t)n * helm::dense_tc_kpad(n)));
     // dense matrix into the left half of aug (row stride 2n): build it in Minv then copy rows
     helm::launch_stencil_to_dense(L, gcst, c->lv[p->levels - 1].coef, c->Minv);
     SETUP_TRY(cudaMemcpy2DAsync(aug, sizeof(c128) * 2 * n, c->Minv, sizeof(c128) * n,
                                 sizeof(c128) * n, n, cudaMemcpyDeviceToDevice, c->st));
     helm::launch_gauss_jordan(L, aug, n, factor, piv, pivval, dstatus);
-    helm::launch_extract_inverse(L, aug, n, c->Minv, c->Minv32);
+    helm::launch_extract_inverse(L, aug, n, c->Minv, nullptr);
+    helm::launch_build_aprime(L, c->Minv, n, c->Ap, p->coarse_tf32x3 != 0);
     int hstatus = 0;
     SETUP_TRY(cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     SETUP_TRY(cudaStreamSynchronize(c->st));
@@ -1003,6 +1014,7 @@ void helm_destroy(helm_ctx* c) {
         dfree(l.coef); dfree(l.dinv); dfree(l.coef32); dfree(l.dinv32);
     }
     dfree(c->cA); dfree(c->cM); dfree(c->cA32); dfree(c->cM32); dfree(c->Minv); dfree(c->Minv32);
+    dfree(c->Ap);
     delete c;
 }
 
@@ -1079,6 +1091,8 @@ helm_status helm_prolong_add(helm_ctx* c, int level, int prec, const void* ec, v
 helm_status helm_coarse_solve(helm_ctx* c, int prec, const void* f, void* u, int s) {
     if (!c || prec < 0 || prec > 1 || !f || !u || s < 1)
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_coarse_solve");
+    helm_status st = ensure_workspace(c, s);
+    if (st != HELM_OK) return st;
     if (prec == 0) coarsest<double>(c, static_cast<const c128*>(f), static_cast<c128*>(u), s);
     else coarsest<float>(c, static_cast<const c64*>(f), static_cast<c64*>(u), s);
     return sync(c);
@@ -1159,6 +1173,9 @@ helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, i
     size_t need = 0;
     for (size_t l = 0; l < c->lv.size(); ++l)
         need += (l == 0 ? 2 : 4) * round256(esz * (size_t)c->lv[l].g.N * (size_t)s);
+    // the complex64 coarsest solve also needs its tensor-core operand scratch
+    const size_t dense_bytes = prec == 1 ? round256(sizeof(float) * helm::dense_tc_scratch_floats(c->nc, s)) : 0;
+    need += dense_bytes;
     if (need > kNoAllocBytes)
         return fail(c, HELM_ERR_ARG,
                     "helm_vcycle_noalloc: " + std::to_string(need) + " bytes of level buffers needed, "
@@ -1177,6 +1194,11 @@ helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, i
         saved[l][2] = c->lv[l].e;  saved[l][3] = c->lv[l].f;
     }
     unsigned char* p = static_cast<unsigned char*>(base);
+    float* saved_dense = c->dense_scratch;
+    if (dense_bytes) {
+        c->dense_scratch = reinterpret_cast<float*>(p);
+        p += dense_bytes;
+    }
     for (size_t l = 0; l < c->lv.size(); ++l) {
         size_t b = round256(esz * (size_t)c->lv[l].g.N * (size_t)s);
         c->lv[l].u0 = p; p += b;
@@ -1193,6 +1215,7 @@ helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, i
         c->lv[l].u0 = saved[l][0]; c->lv[l].u1 = saved[l][1];
         c->lv[l].e = saved[l][2];  c->lv[l].f = saved[l][3];
     }
+    c->dense_scratch = saved_dense;
     return st;
 }
 

@@ -36,7 +36,8 @@ class HelmParams(ctypes.Structure):
                 ("levels", ctypes.c_int), ("pre", ctypes.c_int), ("post", ctypes.c_int),
                 ("jacobi_w", ctypes.c_double), ("restart", ctypes.c_int),
                 ("block", ctypes.c_int), ("max_restarts", ctypes.c_int),
-                ("prec", ctypes.c_int), ("learned_weights", ctypes.c_void_p)]
+                ("prec", ctypes.c_int), ("learned_weights", ctypes.c_void_p),
+                ("coarse_tf32x3", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -126,7 +127,7 @@ class Solver:
     def __init__(self, m, gamma, h: float, omega: float, *, shift: float = 0.5,
                  levels: int = 3, pre: int = 2, post: int = 2, jacobi_w: float = 0.8,
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
-                 prec: str = "c128", stream=None):
+                 prec: str = "c128", stream=None, coarse_tf32x3: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libhelm needs a CUDA device")
@@ -151,6 +152,7 @@ class Solver:
         p.levels, p.pre, p.post, p.jacobi_w = int(levels), int(pre), int(post), float(jacobi_w)
         p.restart, p.block, p.max_restarts = int(restart), int(block), int(max_restarts)
         p.prec = PREC[prec]
+        p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
         self.params = p
         self.prec = prec
         self.stream = stream if stream is not None else torch.cuda.current_stream()
