@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shift", type=float, default=0.2)
-    ap.add_argument("--restart", type=int, default=10)
-    ap.add_argument("--block", type=int, default=8)
+    ap.add_argument("--restart", type=int, default=6)
+    ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--levels", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -90,8 +90,10 @@ typedef struct {
     int block;               /* right-hand sides per Krylov block (>= 1)        */
     int max_restarts;        /* restart cycles before HELM_NOT_CONVERGED        */
     helm_prec prec;          /* precision policy                                */
-    const void* learned_weights; /* device BF16 weights of the learned stage
-                                    (layout in helm_learned.h); NULL = none     */
+    const void* learned_weights; /* device blob of the learned stage (layout:
+                                    helm_learned_layer below), caller-owned,
+                                    must outlive the context; required by
+                                    HELM_MIXED_C64_LEARNED (2D only)            */
     int coarse_tf32x3;       /* complex64 coarsest solve on the tensor cores:
                                 0 = one tf32 product (~1e-3 relative),
                                 1 = three tf32 products on hi/lo splits
@@ -228,6 +230,62 @@ helm_status helm_get_operator(const helm_ctx* ctx, int level, void* coef_host);
 
 /* Number of kernels libhelm launched on this context since set-up. */
 long long helm_kernel_launches(const helm_ctx* ctx);
+
+/* ---------------------------------------------------------------------
+ * Learned preconditioning stage (not in the paper; it relies on FGMRES
+ * accepting a preconditioner that changes from step to step, Sec. 4).
+ * With HELM_MIXED_C64_LEARNED every preconditioner application becomes
+ *     z1 = V-cycle(v);  r = v - A z1 (complex64);  rho_j = RMS of column j;
+ *     z = z1 + h^2 rho_j N(Re r/rho, Im r/rho, omega^2 m h^2)
+ * with N six 3x3 convolutions (ReLU between), 32 hidden channels, BF16
+ * weights and activations, FP32 accumulation on the tensor cores; a
+ * non-finite network output leaves z1 unchanged.
+ * Tensors are NHWC on the 2D node grid: x[b][i][j][c], i the x2 (depth)
+ * node index, j the x1 index; weights [co][tap][ci] with tap = 3 dy + dx
+ * reading pixel (i + dy - 1, j + dx - 1), zero outside the grid.
+ * Weight blob: the bf16 weights of layers 0..5 at byte offsets w_offset,
+ * the float biases at b_offset (256-byte aligned), helm_learned_blob_bytes
+ * in all.  Channels are padded for the tensor-core tiles: layer 0 reads 16
+ * channels (Re r, Im r, kappa, then zeros), layer 5 writes 16 (Re, Im of
+ * the correction, then unused).
+ * ------------------------------------------------------------------- */
+int helm_learned_layers(void);
+long long helm_learned_blob_bytes(void);
+helm_status helm_learned_layer(int layer, int* cin, int* cout, int* relu, long long* w_offset,
+                               long long* b_offset);
+/* y[b][i][j][co] = epilogue(bias[co] + sum_{tap, ci} w[co][tap][ci] x[b][..][ci]);
+   epilogue: ReLU if relu, then zero where mask (bf16, cout channels, may be
+   NULL) is not > 0; y bf16, or float if y_float.  (cin, cout) in {(16,32),
+   (32,32), (32,16), (16,16)}.  All device pointers; enqueued on stream and
+   synchronised.  The data gradient of a layer is this call with the weights
+   from helm_conv3x3_flip and the layer below's activation as the mask. */
+helm_status helm_conv3x3(const void* x, int batch, int H, int W, int cin, const void* w,
+                         const float* bias, int cout, int relu, const void* mask, void* y,
+                         int y_float, void* stream);
+/* dw[co][tap][ci] += sum over pixels gy[co] x[shifted][ci]; db[co] += sum gy[co]
+   (FP32 accumulators, caller zeroes them). */
+helm_status helm_conv3x3_wgrad(const void* x, const void* gy, int batch, int H, int W, int cin,
+                               int cout, float* dw, float* db, void* stream);
+/* wf[ci][tap][co] = w[co][8 - tap][ci] for ci < cin, zero for cin <= ci < cin_out. */
+helm_status helm_conv3x3_flip(const void* w, int cin, int cout, void* wf, int cin_out, void* stream);
+/* Adam step (bias-corrected, step >= 1) on FP32 parameters p with gradient g and
+   moments m, v; p_bf16 (may be NULL) receives the bf16 copy. */
+helm_status helm_adam(float* p, const float* g, float* m, float* v, void* p_bf16, int n, float lr,
+                      float b1, float b2, float eps, int step, void* stream);
+/* Network input for a block: r = f - A z (f complex128, z complex64, internal
+   layout, N x s), rho_out[j] = RMS of column j of r, x_out = bf16 NHWC
+   [s][N2][N1][16].  Allocates its own temporaries. */
+helm_status helm_learned_input(helm_ctx* ctx, const void* f, const void* z, int s, void* x_out,
+                               float* rho_out);
+/* Training target t[j][node][0..1] = scale * e[node][j] / rho[j] (e complex64,
+   internal layout); scale = 1/h^2 makes it the network's output units. */
+helm_status helm_learned_target(const void* e, long long N, int s, const float* rho, float scale,
+                                float* t_out, void* stream);
+/* loss = mean_b ||pred_b - t_b||^2 / ||t_b||^2 (pred: float [B][P][16], channels
+   0, 1 used; t: float [B][P][2]); grad: bf16 [B][P][16]; sums: 2B floats of
+   scratch; loss_out: device float. */
+helm_status helm_learned_loss(const float* pred, const float* t, int batch, long long P, float* sums,
+                              void* grad, float* loss_out, void* stream);
 
 /* ---------------------------------------------------------------------
  * Per-kernel profiler (the per-RHS timing of Sec. 5.3's table, broken down

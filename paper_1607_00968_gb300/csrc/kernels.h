@@ -52,6 +52,39 @@ void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, b
 void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
                      float* scratch, bool split3);
 
+// ---------------- learned stage (learned.cu) ----------------
+
+// y = epilogue(conv3x3(x; w) + bias), NHWC bf16 activations, [co][tap][ci] bf16
+// weights, FP32 accumulation on the tensor cores; (cin, cout) in
+// {(16,32), (32,32), (32,16), (16,16)}; returns false for other shapes.
+bool launch_conv3x3(const Launch& L, const void* x, int B, int H, int W, int cin, const void* w,
+                    const float* bias, int cout, int relu, const void* mask, void* y, int y_float);
+// dw[co][tap][ci] += sum gy x[shifted], db[co] += sum gy (FP32, atomics)
+bool launch_conv3x3_wgrad(const Launch& L, const void* x, const void* gy, int B, int H, int W, int cin,
+                          int cout, float* dw, float* db);
+// wf[ci][tap][co] = w[co][8 - tap][ci] for ci < cin, zero up to cin_pad_out
+void launch_flip_weights(const Launch& L, const void* w, int cin, int cout, void* wf, int cin_pad_out);
+void launch_adam(const Launch& L, float* p, const float* g, float* m, float* v, void* pb, int n,
+                 float lr, float b1, float b2, float eps, int step);
+void launch_pack_input(const Launch& L, const c64* r, int N, int s, const float* rho,
+                       const float* kappa, void* out);
+void launch_unpack_add(const Launch& L, const float* out, int N, int s, const float* rho, float scale,
+                       c64* z);
+// kappa[i] = Re(cA[i]) h^2 = omega^2 m_i h^2 (the network's third input channel)
+void launch_kappa(const Launch& L, const c128* cA, long long N, double h2, float* kappa);
+void launch_pack_target(const Launch& L, const c64* e, int N, int s, const float* rho, float scale,
+                        float* t);
+// loss = mean_b ||pred_b - t_b||^2 / ||t_b||^2 over channels 0, 1 (pred: 16-channel
+// float NHWC, t: 2-channel float), grad (bf16, 16 channels) and loss_out (device float)
+void launch_loss(const Launch& L, const float* pred, const float* t, int B, int P, float* sums,
+                 void* grad, float* loss_out);
+// z1[:, j] = z2[:, j] where sum |r2|^2 (r2sq[j]) < N rho1[j]^2
+void launch_select_better(const Launch& L, const c64* z2, c64* z1, long long N, int s,
+                          const float* rho1, const float* r2sq);
+// r = f - A z (complex64) and rho[j] = RMS of column j of r
+void launch_learned_residual(const Launch& L, const FineOp<float>& op, const c128* f, const c64* z,
+                             c64* r, int s, float* rho2, float* rho);
+
 // ---------------- set-up (mg.cu) ----------------
 
 // c_A = omega^2 m (1 - i gamma), c_M = omega^2 m (1 - i (gamma + shift)),

@@ -133,6 +133,16 @@ struct helm_ctx {
     c64* Minv32 = nullptr;
     float* Ap = nullptr;      // tf32-rounded interleaved inverse for the tensor-core solve
     float* dense_scratch = nullptr;
+    // learned stage
+    float* kappa = nullptr;   // omega^2 m h^2 per node
+    c64* lr_r = nullptr;      // residual of the cycle's result
+    float* lr_rho2 = nullptr;
+    float* lr_rho = nullptr;
+    void* lr_x0 = nullptr;    // bf16 network input, 16 channels
+    void* lr_act[2] = {nullptr, nullptr};  // bf16 activations, 32 channels
+    float* lr_out = nullptr;  // float network output, 16 channels
+    c64* lr_z2 = nullptr;     // corrected block before the acceptance test
+    float* lr_rho_new = nullptr;
     // Krylov workspace, sized for s_cap columns
     int s_cap = 0;
     c128* V = nullptr;       // (restart+1) blocks of N x s
@@ -308,6 +318,12 @@ void free_workspace(helm_ctx* c) {
     c->csplit = nullptr;
     dfree(c->dense_scratch);
     c->dense_scratch = nullptr;
+    dfree(c->lr_r); dfree(c->lr_rho2); dfree(c->lr_rho); dfree(c->lr_x0);
+    dfree(c->lr_act[0]); dfree(c->lr_act[1]); dfree(c->lr_out);
+    dfree(c->lr_z2); dfree(c->lr_rho_new);
+    c->lr_z2 = nullptr; c->lr_rho_new = nullptr;
+    c->lr_r = nullptr; c->lr_rho2 = c->lr_rho = nullptr; c->lr_x0 = nullptr;
+    c->lr_act[0] = c->lr_act[1] = nullptr; c->lr_out = nullptr;
     if (c->hsmall) cudaFreeHost(c->hsmall);
     c->V = c->W = c->W2 = c->Bint = c->X = c->R = c->abi_in = c->abi_out = c->partial = c->small =
         nullptr;
@@ -355,6 +371,17 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
     CUDA_TRY(c, dalloc(&c->csplit, sizeof(float4) * (size_t)(m + 1) * blk));
     CUDA_TRY(c, dalloc(&c->dense_scratch, sizeof(float) * helm::dense_tc_scratch_floats(c->nc, s)));
+    if (c->p.prec == HELM_MIXED_C64_LEARNED) {
+        CUDA_TRY(c, dalloc(&c->lr_r, sizeof(c64) * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_rho2, sizeof(float) * s));
+        CUDA_TRY(c, dalloc(&c->lr_rho, sizeof(float) * s));
+        CUDA_TRY(c, dalloc(&c->lr_x0, 2 * 16 * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_act[0], 2 * 32 * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_act[1], 2 * 32 * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_out, 4 * 16 * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_z2, sizeof(c64) * (size_t)N * s));
+        CUDA_TRY(c, dalloc(&c->lr_rho_new, sizeof(float) * s));
+    }
     c->s_cap = s;
     return HELM_OK;
 }
@@ -644,6 +671,54 @@ helm_status colnorms(helm_ctx* c, const c128* X, int s, std::vector<double>& out
 }
 
 // ---------------------------------------------------------------------------
+// learned stage: z <- z + h^2 rho N(r / rho, kappa), r = v - A z
+// ---------------------------------------------------------------------------
+
+struct LearnedLayer { int cin, cout, relu; long long w_off, b_off; };
+
+// Six 3x3 layers, channels padded for the tensor-core tiles: input 3 -> 16
+// (Re r, Im r, kappa), 32 hidden channels, output 2 -> 16 (Re e, Im e).
+// Blob: all bf16 weights [co][tap][ci] back to back, then the float biases.
+const LearnedLayer* learned_table() {
+    static LearnedLayer t[6];
+    static bool init = false;
+    if (!init) {
+        const int cin[6] = {16, 32, 32, 32, 32, 32}, cout[6] = {32, 32, 32, 32, 32, 16};
+        long long w = 0;
+        for (int l = 0; l < 6; ++l) { t[l].cin = cin[l]; t[l].cout = cout[l]; t[l].relu = l < 5; t[l].w_off = w; w += 2LL * cout[l] * 9 * cin[l]; }
+        long long b = (w + 255) / 256 * 256;
+        for (int l = 0; l < 6; ++l) { t[l].b_off = b; b += 4LL * cout[l]; }
+        init = true;
+    }
+    return t;
+}
+long long learned_blob_bytes() { return learned_table()[5].b_off + 4LL * 16; }
+
+void learned_stage(helm_ctx* c, const c128* v, c64* z, int s) {
+    const long long N = c->N();
+    const Grid& g = c->lv[0].g;
+    helm::launch_learned_residual(c->L(), fine_op<float>(c, false), v, z, c->lr_r, s, c->lr_rho2, c->lr_rho);
+    helm::launch_pack_input(c->L(), c->lr_r, (int)N, s, c->lr_rho, c->kappa, c->lr_x0);
+    const unsigned char* blob = static_cast<const unsigned char*>(c->p.learned_weights);
+    const LearnedLayer* T = learned_table();
+    const void* in = c->lr_x0;
+    for (int l = 0; l < 6; ++l) {
+        void* out = l == 5 ? static_cast<void*>(c->lr_out) : c->lr_act[l % 2];
+        helm::launch_conv3x3(c->L(), in, s, g.n2, g.n1, T[l].cin, blob + T[l].w_off,
+                             reinterpret_cast<const float*>(blob + T[l].b_off), T[l].cout, T[l].relu,
+                             nullptr, out, l == 5);
+        in = out;
+    }
+    // z2 = z + correction; keep it only for the columns whose residual
+    // ||v - A z2|| is below ||v - A z|| (the plain cycle is the fallback)
+    cudaMemcpyAsync(c->lr_z2, z, sizeof(c64) * (size_t)N * s, cudaMemcpyDeviceToDevice, c->st);
+    helm::launch_unpack_add(c->L(), c->lr_out, (int)N, s, c->lr_rho, (float)(c->p.h * c->p.h), c->lr_z2);
+    helm::launch_learned_residual(c->L(), fine_op<float>(c, false), v, c->lr_z2, c->lr_r, s,
+                                  c->lr_rho_new, c->lr_rho2 /* receives the new RMS; unused */);
+    helm::launch_select_better(c->L(), c->lr_z2, z, N, s, c->lr_rho, c->lr_rho_new);
+}
+
+// ---------------------------------------------------------------------------
 // block FGMRES (Sec. 5.3)
 // ---------------------------------------------------------------------------
 
@@ -712,6 +787,8 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
             // Z_j = M^{-1}_cycle V_j ; W = A Z_j
             cplx<ZT>* Zj = Z + (long long)j * vs;
             cycle<ZT, double>(c, 0, c->V + (long long)j * vs, Zj, s);
+            if constexpr (std::is_same<ZT, float>::value)
+                if (c->p.prec == HELM_MIXED_C64_LEARNED) learned_stage(c, c->V + (long long)j * vs, Zj, s);
             helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), opA, Zj, c->W, s);
             c128* H1 = c->small + SL.oH1;
             c128* H2 = c->small + SL.oH2;
@@ -863,6 +940,8 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         return fail(nullptr, HELM_ERR_ARG, "bad parameter");
     if (p->prec != HELM_PLAIN_C128 && p->prec != HELM_MIXED_C64 && p->prec != HELM_MIXED_C64_LEARNED)
         return fail(nullptr, HELM_ERR_ARG, "bad precision policy");
+    if (p->prec == HELM_MIXED_C64_LEARNED && (p->dim != 2 || !p->learned_weights))
+        return fail(nullptr, HELM_ERR_ARG, "the learned stage needs a 2D grid and learned_weights");
     int nodes[3] = {1, 1, 1};
     for (int k = 0; k < p->dim; ++k) {
         if (p->n[k] < 1) return fail(nullptr, HELM_ERR_ARG, "cells per axis must be >= 1");
@@ -920,6 +999,8 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         helm::launch_galerkin(L, c->lv[l - 1].g, c->lv[l].g, c->lv[l - 1].coef, c->lv[l].coef);
         helm::launch_diag_inv(L, c->lv[l].g, c->lv[l].coef, c->lv[l].dinv);
     }
+    SETUP_TRY(dalloc(&c->kappa, sizeof(float) * N0));
+    helm::launch_kappa(L, c->cA, N0, p->h * p->h, c->kappa);
     helm::launch_round_c64(L, c->cA, c->cA32, N0);
     helm::launch_round_c64(L, c->cM, c->cM32, N0);
     for (int l = 0; l < p->levels; ++l) {
@@ -1015,6 +1096,7 @@ void helm_destroy(helm_ctx* c) {
     }
     dfree(c->cA); dfree(c->cM); dfree(c->cA32); dfree(c->cM32); dfree(c->Minv); dfree(c->Minv32);
     dfree(c->Ap);
+    dfree(c->kappa);
     delete c;
 }
 
@@ -1224,7 +1306,8 @@ long long helm_kernel_launches(const helm_ctx* c) { return c ? c->launches : 0; 
 static const char* kKernelNames[helm::KID_COUNT] = {
     "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",
     "restrict_fine", "restrict_coarse", "prolong_add", "coarsest_dense", "gram", "gram_reduce",
-    "combine", "layout", "random_fill", "setup", "gram_dd", "combine_dd"};
+    "combine", "layout", "random_fill", "setup", "gram_dd", "combine_dd", "conv3x3",
+    "conv3x3_wgrad"};
 
 helm_status helm_profile_enable(helm_ctx* c, int enable) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
@@ -1236,6 +1319,101 @@ helm_status helm_profile_enable(helm_ctx* c, int enable) {
         c->prof = nullptr;
     }
     return HELM_OK;
+}
+
+int helm_learned_layers(void) { return 6; }
+
+long long helm_learned_blob_bytes(void) { return learned_blob_bytes(); }
+
+helm_status helm_learned_layer(int layer, int* cin, int* cout, int* relu, long long* w_offset,
+                               long long* b_offset) {
+    if (layer < 0 || layer >= 6) return fail(nullptr, HELM_ERR_ARG, "bad layer");
+    const LearnedLayer& t = learned_table()[layer];
+    if (cin) *cin = t.cin;
+    if (cout) *cout = t.cout;
+    if (relu) *relu = t.relu;
+    if (w_offset) *w_offset = t.w_off;
+    if (b_offset) *b_offset = t.b_off;
+    return HELM_OK;
+}
+
+static Launch bare_launch(void* stream) {
+    return Launch{reinterpret_cast<cudaStream_t>(stream), nullptr, nullptr};
+}
+
+static helm_status check_launch(void* stream) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, HELM_ERR_CUDA, cudaGetErrorString(e));
+    return HELM_OK;
+}
+
+helm_status helm_conv3x3(const void* x, int batch, int H, int W, int cin, const void* w,
+                         const float* bias, int cout, int relu, const void* mask, void* y,
+                         int y_float, void* stream) {
+    if (!x || !w || !y || batch < 1 || H < 1 || W < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_conv3x3");
+    if (!helm::launch_conv3x3(bare_launch(stream), x, batch, H, W, cin, w, bias, cout, relu, mask, y,
+                              y_float))
+        return fail(nullptr, HELM_ERR_ARG, "unsupported channel counts for helm_conv3x3");
+    return check_launch(stream);
+}
+
+helm_status helm_conv3x3_wgrad(const void* x, const void* gy, int batch, int H, int W, int cin,
+                               int cout, float* dw, float* db, void* stream) {
+    if (!x || !gy || !dw || !db || batch < 1 || H < 1 || W < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_conv3x3_wgrad");
+    if (!helm::launch_conv3x3_wgrad(bare_launch(stream), x, gy, batch, H, W, cin, cout, dw, db))
+        return fail(nullptr, HELM_ERR_ARG, "unsupported channel counts for helm_conv3x3_wgrad");
+    return check_launch(stream);
+}
+
+helm_status helm_conv3x3_flip(const void* w, int cin, int cout, void* wf, int cin_out, void* stream) {
+    if (!w || !wf || cin < 1 || cout < 1 || cin_out < cin)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_conv3x3_flip");
+    helm::launch_flip_weights(bare_launch(stream), w, cin, cout, wf, cin_out);
+    return check_launch(stream);
+}
+
+helm_status helm_adam(float* p, const float* g, float* m, float* v, void* p_bf16, int n, float lr,
+                      float b1, float b2, float eps, int step, void* stream) {
+    if (!p || !g || !m || !v || n < 1 || step < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_adam");
+    helm::launch_adam(bare_launch(stream), p, g, m, v, p_bf16, n, lr, b1, b2, eps, step);
+    return check_launch(stream);
+}
+
+helm_status helm_learned_input(helm_ctx* c, const void* f, const void* z, int s, void* x_out,
+                               float* rho_out) {
+    if (!c || !f || !z || !x_out || !rho_out || s < 1 || c->p.dim != 2)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_learned_input");
+    c64* r = nullptr;
+    float* rho2 = nullptr;
+    CUDA_TRY(c, dalloc(&r, sizeof(c64) * (size_t)c->N() * s));
+    CUDA_TRY(c, dalloc(&rho2, sizeof(float) * s));
+    helm::launch_learned_residual(c->L(), fine_op<float>(c, false), static_cast<const c128*>(f),
+                                  static_cast<const c64*>(z), r, s, rho2, rho_out);
+    helm::launch_pack_input(c->L(), r, (int)c->N(), s, rho_out, c->kappa, x_out);
+    helm_status st = sync(c);
+    dfree(r);
+    dfree(rho2);
+    return st;
+}
+
+helm_status helm_learned_target(const void* e, long long N, int s, const float* rho, float scale,
+                                float* t_out, void* stream) {
+    if (!e || !rho || !t_out || N < 1 || s < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_learned_target");
+    helm::launch_pack_target(bare_launch(stream), static_cast<const c64*>(e), (int)N, s, rho, scale, t_out);
+    return check_launch(stream);
+}
+
+helm_status helm_learned_loss(const float* pred, const float* t, int batch, long long P, float* sums,
+                              void* grad, float* loss_out, void* stream) {
+    if (!pred || !t || !sums || !grad || batch < 1 || P < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_learned_loss");
+    helm::launch_loss(bare_launch(stream), pred, t, batch, (int)P, sums, grad, loss_out);
+    return check_launch(stream);
 }
 
 int helm_profile_kernel_count(void) { return helm::KID_COUNT; }

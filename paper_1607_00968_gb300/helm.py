@@ -27,7 +27,10 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_apply", "helm_smooth", "helm_restrict_residual", "helm_prolong_add",
            "helm_coarse_solve", "helm_vcycle", "helm_get_operator", "helm_kernel_launches",
            "helm_profile_enable", "helm_profile_kernel_count", "helm_profile_kernel_name",
-           "helm_profile_read", "helm_vcycle_noalloc"]
+           "helm_profile_read", "helm_vcycle_noalloc", "helm_learned_layers",
+           "helm_learned_blob_bytes", "helm_learned_layer", "helm_conv3x3", "helm_conv3x3_wgrad",
+           "helm_conv3x3_flip", "helm_adam", "helm_learned_input", "helm_learned_target",
+           "helm_learned_loss"]
 
 
 class HelmParams(ctypes.Structure):
@@ -89,6 +92,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_profile_kernel_count": (i, []),
         "helm_profile_kernel_name": (ctypes.c_char_p, [i]),
         "helm_profile_read": (i, [vp, i, P(d), P(ll), P(d), P(d)]),
+        "helm_learned_layers": (i, []),
+        "helm_learned_blob_bytes": (ll, []),
+        "helm_learned_layer": (i, [i, P(i), P(i), P(i), P(ll), P(ll)]),
+        "helm_conv3x3": (i, [vp, i, i, i, i, vp, vp, i, i, vp, vp, i, vp]),
+        "helm_conv3x3_wgrad": (i, [vp, vp, i, i, i, i, i, vp, vp, vp]),
+        "helm_conv3x3_flip": (i, [vp, i, i, vp, i, vp]),
+        "helm_adam": (i, [vp, vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                          ctypes.c_float, i, vp]),
+        "helm_learned_input": (i, [vp, vp, vp, i, vp, vp]),
+        "helm_learned_target": (i, [vp, ll, i, vp, ctypes.c_float, vp, vp]),
+        "helm_learned_loss": (i, [vp, vp, i, ll, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,7 +141,8 @@ class Solver:
     def __init__(self, m, gamma, h: float, omega: float, *, shift: float = 0.5,
                  levels: int = 3, pre: int = 2, post: int = 2, jacobi_w: float = 0.8,
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
-                 prec: str = "c128", stream=None, coarse_tf32x3: bool = False):
+                 prec: str = "c128", stream=None, coarse_tf32x3: bool = False,
+                 learned_weights=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libhelm needs a CUDA device")
@@ -153,6 +168,8 @@ class Solver:
         p.restart, p.block, p.max_restarts = int(restart), int(block), int(max_restarts)
         p.prec = PREC[prec]
         p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
+        self.learned_weights = learned_weights        # keeps the blob alive
+        p.learned_weights = _ptr(learned_weights) if learned_weights is not None else None
         self.params = p
         self.prec = prec
         self.stream = stream if stream is not None else torch.cuda.current_stream()

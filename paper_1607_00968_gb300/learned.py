@@ -1,0 +1,297 @@
+"""Learned preconditioning stage: network state, training data, training loop.
+
+The network (six 3x3 convolutions, 32 hidden channels, ReLU between) maps the
+residual left by one shifted-Laplacian V-cycle, r = v - A V(v), normalised by
+its RMS rho, plus kappa = omega^2 m h^2, to a correction e ~ A^{-1} r in units
+of h^2 rho; FGMRES then uses z = V(v) + h^2 rho N(r/rho, kappa) (see
+include/helm.h, "Learned preconditioning stage").  Every forward, backward,
+loss and optimiser step runs in libhelm's kernels (helm_conv3x3,
+helm_conv3x3_wgrad, helm_conv3x3_flip, helm_learned_loss, helm_adam); this
+module holds the buffers and drives the loop.
+
+Training pairs come from the solver itself on seeded random faulted/salt
+models: for right-hand sides v taken along two chains started at the point
+sources (the residuals of the stationary iteration x <- x + V(b - A x), and a
+one-vector Arnoldi process on A V), the target is e = A^{-1} v - V(v), with
+A^{-1} v from a tight solve.
+
+Weights are saved as the flat blob of the ABI (bf16 weights + float biases)
+plus a JSON header (layer table, training record).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import helm, inputs
+
+
+def _vp(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class Network:
+    """Device-resident network: the ABI weight blob (bf16 weights, float
+    biases; the biases in the blob are the master copies), FP32 master
+    weights, gradients and Adam moments."""
+
+    def __init__(self, seed: int = 0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.lib = helm.load()
+        L = self.lib
+        self.layers = []
+        for l in range(L.helm_learned_layers()):
+            cin, cout, relu = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            wo, bo = ctypes.c_longlong(), ctypes.c_longlong()
+            L.helm_learned_layer(l, ctypes.byref(cin), ctypes.byref(cout), ctypes.byref(relu),
+                                 ctypes.byref(wo), ctypes.byref(bo))
+            self.layers.append(dict(cin=cin.value, cout=cout.value, relu=relu.value,
+                                    w_off=wo.value, b_off=bo.value))
+        self.blob = torch.zeros(int(L.helm_learned_blob_bytes()), dtype=torch.uint8, device=device)
+        g = np.random.Generator(np.random.PCG64(seed))
+        self.w32, self.wbf, self.b, self.dw, self.db, self.mom = [], [], [], [], [], []
+        for l, t in enumerate(self.layers):
+            n = t["cout"] * 9 * t["cin"]
+            used_in = 3 if l == 0 else t["cin"]
+            used_out = 2 if l == len(self.layers) - 1 else t["cout"]
+            w = np.zeros((t["cout"], 9, t["cin"]), dtype=np.float32)
+            std = math.sqrt(2.0 / (9 * used_in))
+            if l == len(self.layers) - 1:
+                std *= 0.1                       # start close to the plain cycle
+            w[:used_out, :, :used_in] = g.standard_normal((used_out, 9, used_in)) * std
+            w32 = torch.as_tensor(w.reshape(-1)).to(device)
+            wbf = self.blob[t["w_off"]:t["w_off"] + 2 * n].view(torch.bfloat16)
+            wbf.copy_(w32.to(torch.bfloat16))
+            b = self.blob[t["b_off"]:t["b_off"] + 4 * t["cout"]].view(torch.float32)
+            self.w32.append(w32)
+            self.wbf.append(wbf)
+            self.b.append(b)
+            self.dw.append(torch.zeros_like(w32))
+            self.db.append(torch.zeros_like(b))
+            self.mom.append([torch.zeros_like(w32), torch.zeros_like(w32),
+                             torch.zeros_like(b), torch.zeros_like(b)])
+        self.flip = [torch.empty(t["cin"] * 9 * t["cout"], dtype=torch.bfloat16, device=device)
+                     for t in self.layers]
+        self.step_count = 0
+        self.record = {}
+
+    # ------------------------------------------------------------------
+    def _check(self, st, what):
+        if st != 0:
+            raise helm.HelmError(st, what + ": " + self.lib.helm_last_error(None).decode())
+
+    def forward(self, x, B, H, W, keep=False):
+        """x: bf16 [B, H, W, 16] -> float [B, H, W, 16] (channels 0, 1 used)."""
+        torch = self.torch
+        stream = _vp_stream(torch)
+        acts = [x]
+        cur = x
+        for l, t in enumerate(self.layers):
+            last = l == len(self.layers) - 1
+            out = torch.empty((B, H, W, t["cout"]), device=x.device,
+                              dtype=torch.float32 if last else torch.bfloat16)
+            self._check(self.lib.helm_conv3x3(_vp(cur), B, H, W, t["cin"], _vp(self.wbf[l]),
+                                              _vp(self.b[l]), t["cout"], t["relu"], None, _vp(out),
+                                              1 if last else 0, stream), "conv3x3")
+            acts.append(out)
+            cur = out
+        return (cur, acts) if keep else cur
+
+    def backward(self, acts, grad, B, H, W):
+        """grad: bf16 [B, H, W, 16], d loss / d output.  Accumulates dw, db."""
+        torch = self.torch
+        stream = _vp_stream(torch)
+        g = grad
+        for l in range(len(self.layers) - 1, -1, -1):
+            t = self.layers[l]
+            self._check(self.lib.helm_conv3x3_wgrad(_vp(acts[l]), _vp(g), B, H, W, t["cin"],
+                                                    t["cout"], _vp(self.dw[l]), _vp(self.db[l]),
+                                                    stream), "wgrad")
+            if l == 0:
+                break
+            self._check(self.lib.helm_conv3x3_flip(_vp(self.wbf[l]), t["cin"], t["cout"],
+                                                   _vp(self.flip[l]), t["cin"], stream), "flip")
+            gin = torch.empty((B, H, W, t["cin"]), device=g.device, dtype=torch.bfloat16)
+            # data gradient: conv with transposed, flipped weights, times the
+            # ReLU derivative of the layer below (its output > 0)
+            self._check(self.lib.helm_conv3x3(_vp(g), B, H, W, t["cout"], _vp(self.flip[l]), None,
+                                              t["cin"], 0, _vp(acts[l]), _vp(gin), 0, stream),
+                        "conv3x3 backward")
+            g = gin
+
+    def zero_grad(self):
+        for a in self.dw + self.db:
+            a.zero_()
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step_count += 1
+        stream = _vp_stream(self.torch)
+        for l in range(len(self.layers)):
+            m1, v1, m2, v2 = self.mom[l]
+            self._check(self.lib.helm_adam(_vp(self.w32[l]), _vp(self.dw[l]), _vp(m1), _vp(v1),
+                                           _vp(self.wbf[l]), self.w32[l].numel(), lr, b1, b2, eps,
+                                           self.step_count, stream), "adam")
+            self._check(self.lib.helm_adam(_vp(self.b[l]), _vp(self.db[l]), _vp(m2), _vp(v2), None,
+                                           self.b[l].numel(), lr, b1, b2, eps, self.step_count,
+                                           stream), "adam")
+
+    # ------------------------------------------------------------------
+    def save(self, path: str):
+        """Flat blob (bytes of the ABI layout) + JSON header next to it."""
+        with open(path, "wb") as f:
+            f.write(self.blob.cpu().numpy().tobytes())
+        head = dict(layers=self.layers, blob_bytes=int(self.blob.numel()), record=self.record,
+                    format="libhelm learned-stage blob: bf16 weights [co][tap][ci], float biases")
+        with open(path + ".json", "w") as f:
+            json.dump(head, f, indent=1)
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        net = cls(seed=0, device=device)
+        raw = np.frombuffer(open(path, "rb").read(), dtype=np.uint8)
+        if raw.size != net.blob.numel():
+            raise ValueError("weight blob size %d does not match the layer table (%d)"
+                             % (raw.size, net.blob.numel()))
+        net.blob.copy_(net.torch.as_tensor(raw.copy()).to(device))
+        for l in range(len(net.layers)):
+            net.w32[l].copy_(net.wbf[l].float())
+        hp = path + ".json"
+        if os.path.exists(hp):
+            net.record = json.load(open(hp)).get("record", {})
+        return net
+
+
+def _vp_stream(torch):
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ----------------------------------------------------------------------
+# training data from the solver
+# ----------------------------------------------------------------------
+
+def make_pairs(seeds, freqs, cells=(512, 256), h=12.5, nsrc=32, steps=2, shift=0.2, levels=3,
+               tol=1e-7, chains=("residual", "arnoldi")):
+    """Returns (x bf16 [P, H, W, 16], t float [P, H, W, 2]) on the device.
+
+    Right-hand sides start at the normalised point sources and follow one or
+    both chains: "residual", v <- (v - A V(v)) normalised (the residuals of
+    the stationary iteration), and "arnoldi", v <- A V(v) orthogonalised
+    against v and normalised (one-vector Arnoldi, closer to the FGMRES
+    basis vectors)."""
+    import torch
+    lib = helm.load()
+    xs, ts = [], []
+    for seed in seeds:
+        for f in freqs:
+            P = inputs.random_problem_2d(seed, cells, h, f, nsrc, width=20, levels=levels)
+            S = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=shift, levels=levels, block=8,
+                            restart=10, prec="c64", max_restarts=200)
+            N = S.N
+            H, W = P.shape
+            b = torch.as_tensor(P.rhs()).cuda()                    # (s, N) ABI layout
+            for chain in chains:
+              v = (b / torch.linalg.vector_norm(b, dim=1, keepdim=True)).T.contiguous()  # (N, s)
+              for k in range(steps):
+                  z1 = S.vcycle(v, "c64")                            # (N, s) complex64
+                  x = torch.empty((nsrc, H, W, 16), dtype=torch.bfloat16, device="cuda")
+                  rho = torch.empty(nsrc, dtype=torch.float32, device="cuda")
+                  st = lib.helm_learned_input(S.ctx, _vp(v), _vp(z1), nsrc, _vp(x), _vp(rho))
+                  if st != 0:
+                      raise helm.HelmError(st, lib.helm_last_error(S.ctx).decode())
+                  u, info, _ = S.solve(v.T.contiguous(), tol)        # A^{-1} v, (s, N)
+                  e = (u.T - z1.to(torch.complex128)).to(torch.complex64).contiguous()
+                  t = torch.empty((nsrc, H, W, 2), dtype=torch.float32, device="cuda")
+                  st = lib.helm_learned_target(_vp(e), N, nsrc, _vp(rho), 1.0 / (h * h), _vp(t),
+                                               _vp_stream(torch))
+                  if st != 0:
+                      raise helm.HelmError(st, lib.helm_last_error(None).decode())
+                  xs.append(x)
+                  ts.append(t)
+                  Az = S.apply(z1.to(torch.complex128), 0, "A")
+                  if chain == "residual":
+                      r = v - Az
+                  else:
+                      r = Az - v * (v.conj() * Az).sum(dim=0, keepdim=True)
+                  v = (r / torch.linalg.vector_norm(r, dim=0, keepdim=True)).contiguous()
+            S.close()
+    return torch.cat(xs), torch.cat(ts)
+
+
+def train(net: Network, x, t, iters=400, batch=8, lr=1e-3, seed=0, log_every=50):
+    """Adam on mini-batches of whole images; returns the loss history."""
+    import torch
+    lib = net.lib
+    P, H, W, _ = x.shape
+    g = np.random.Generator(np.random.PCG64(seed))
+    sums = torch.empty(2 * batch, dtype=torch.float32, device=x.device)
+    loss_d = torch.empty(1, dtype=torch.float32, device=x.device)
+    grad = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=x.device)
+    hist = []
+    t0 = time.perf_counter()
+    for it in range(iters):
+        idx = torch.as_tensor(g.choice(P, size=batch, replace=False), device=x.device)
+        xb, tb = x[idx].contiguous(), t[idx].contiguous()
+        out, acts = net.forward(xb, batch, H, W, keep=True)
+        st = lib.helm_learned_loss(_vp(out), _vp(tb), batch, H * W, _vp(sums), _vp(grad),
+                                   _vp(loss_d), _vp_stream(torch))
+        if st != 0:
+            raise helm.HelmError(st, lib.helm_last_error(None).decode())
+        net.zero_grad()
+        net.backward(acts, grad, batch, H, W)
+        net.adam(lr=lr)
+        if it % log_every == 0 or it == iters - 1:
+            hist.append((it, float(loss_d.item())))
+    net.record.update(dict(iters=iters, batch=batch, lr=lr, pairs=int(P),
+                           seconds=time.perf_counter() - t0, loss_history=hist))
+    return hist
+
+
+def evaluate_loss(net: Network, x, t, batch=8):
+    import torch
+    P, H, W, _ = x.shape
+    lib = net.lib
+    tot = 0.0
+    n = 0
+    sums = torch.empty(2 * batch, dtype=torch.float32, device=x.device)
+    loss_d = torch.empty(1, dtype=torch.float32, device=x.device)
+    grad = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=x.device)
+    for i0 in range(0, P - batch + 1, batch):
+        out = net.forward(x[i0:i0 + batch].contiguous(), batch, H, W)
+        lib.helm_learned_loss(_vp(out), _vp(t[i0:i0 + batch].contiguous()), batch, H * W,
+                              _vp(sums), _vp(grad), _vp(loss_d), _vp_stream(torch))
+        tot += float(loss_d.item())
+        n += 1
+    return tot / max(n, 1)
+
+
+def main():
+    """Train the stage on seeded models and save the blob:
+    python -m paper_1607_00968_gb300.learned OUT_PATH [ITERS]"""
+    import sys
+    import torch
+    out = sys.argv[1] if len(sys.argv) > 1 else "learned_salt2d.bin"
+    iters = int(sys.argv[2]) if len(sys.argv) > 2 else 600
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    x, t = make_pairs(seeds=(101, 102, 103), freqs=(3.5, 5.0, 6.5), nsrc=32, steps=3)
+    xv, tv = make_pairs(seeds=(201,), freqs=(5.0,), nsrc=16, steps=3)
+    gen = time.perf_counter() - t0
+    net = Network(seed=0)
+    before = evaluate_loss(net, xv, tv)
+    hist = train(net, x, t, iters=iters)
+    after = evaluate_loss(net, xv, tv)
+    net.record.update(dict(data_seconds=gen, val_loss_before=before, val_loss_after=after,
+                           train_seeds=[101, 102, 103], val_seeds=[201],
+                           train_freqs_hz=[3.5, 5.0, 6.5], cells=[512, 256], h=12.5))
+    net.save(out)
+    print(json.dumps(net.record))
+
+
+if __name__ == "__main__":
+    main()
