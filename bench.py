@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the complex128 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", default="salt2d",
+                    choices=["salt2d", "layered2d", "layered3d", "batch"],
+                    help="salt2d: the default line; the others are the small 2D, the 3D and the "
+                         "uneven-batch configurations, measured with the same timing rules")
+    ap.add_argument("--problems", type=int, default=40, help="batch workload: number of problems")
     return ap.parse_args()
 
 
@@ -240,10 +245,98 @@ def timed_steps(torch, solvers, Qd, steps, stream):
     return a.elapsed_time(b), infos
 
 
+# --------------------------------------------------------------------------
+# the other configurations (small 2D, 3D, uneven batch)
+# --------------------------------------------------------------------------
+
+def run_other(args):
+    import torch
+    from paper_1607_00968_gb300 import helm, inputs
+    torch.cuda.set_device(0)
+    line = {"unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    if args.workload in ("layered2d", "layered3d"):
+        if args.workload == "layered2d":
+            P = inputs.layered2d_problem(seed=args.seed)
+            kw = dict(levels=3, restart=10, block=8, shift=0.5)
+            runs = [("c128", "complex128, shift 0.5, 3 levels, V(2,2), FGMRES(10), block 8"),
+                    ("c64", "complex64 cycle + FP64 Krylov")]
+            desc = "layered2d_128x64_8src_6Hz"
+        else:
+            P = inputs.layered3d_problem(seed=args.seed)
+            kw = dict(levels=4, restart=5, block=32, shift=0.5)
+            runs = [("c64", "complex64 cycle + FP64 Krylov, shift 0.5, 4 levels, FGMRES(5), "
+                            "block 32 (8 groups in lock step)")]
+            desc = "layered3d_128x128x64_256src_4Hz"
+        Q = torch.as_tensor(P.rhs()).cuda()
+        res = {}
+        for prec, what in runs:
+            S = helm.Solver(P.m, P.gamma, P.h, P.omega, prec=prec, max_restarts=200, **kw)
+            for _ in range(args.warmup):
+                S.solve(Q, TOL)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.steps):
+                U, info, st = S.solve(Q, TOL)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / args.steps
+            res[prec] = {"value": Q.shape[0] / (ms / 1e3), "ms_per_step": ms, "what": what,
+                         "cycles": int(info.iters.max()), "max_relres": float(info.relres.max()),
+                         "kernel_launches_per_step": None}
+            S.close()
+        head = runs[-1][0]
+        line.update({"metric": "Helmholtz RHS-solves/s to rel-res 1e-6 (%s)" % desc,
+                     "value": round(res[head]["value"], 3), "ms_per_step": res[head]["ms_per_step"],
+                     "dtype": "c64+f64" if head == "c64" else "c128",
+                     "config": dict(workload=desc, nodes=P.n_nodes, sources=Q.shape[0],
+                                    omega=P.omega, **kw), "runs": res})
+    else:
+        rng = np.random.Generator(np.random.PCG64(args.seed))
+        grids = [(256, 128), (512, 256), (1024, 512)]
+        solvers, Qs, meta = [], [], []
+        for k in range(args.problems):
+            cells = grids[rng.integers(0, 3)]
+            f = float(rng.uniform(2.0, 10.0))
+            s = int(rng.integers(1, 129))
+            prec = "c64" if rng.uniform() < 0.5 else "c128"
+            # fewest levels whose coarsest grid has <= 9000 nodes (dense
+            # inverse); the FP64 path keeps <= 2200 to bound its set-up
+            lv = inputs.default_levels(cells, 9000 if prec == "c64" else 2200)
+            P = inputs.random_problem_2d(1000 + k, cells, 12.5, f, s, width=20, levels=lv)
+            st = torch.cuda.Stream()
+            solvers.append(helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, levels=lv,
+                                       block=args.block, restart=args.restart, prec=prec,
+                                       max_restarts=300, stream=st))
+            Qs.append(torch.as_tensor(P.rhs()).cuda())
+            meta.append(dict(cells=cells, f=round(f, 2), s=s, prec=prec, levels=lv))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Us, infos, st = helm.solve_batch(solvers, Qs, TOL, check=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        tot = sum(q.shape[0] for q in Qs)
+        conv = sum(int(np.all(i.relres <= TOL)) for i in infos)
+        line.update({"metric": "Helmholtz RHS-solves/s to rel-res 1e-6 (uneven batch of %d 2D problems)"
+                               % args.problems,
+                     "value": round(tot / wall, 3), "ms_per_step": wall * 1e3, "steps": 1,
+                     "warmup": 0, "dtype": "mixed c64/c128",
+                     "config": dict(workload="batch%d_2d_uneven" % args.problems, rhs=tot,
+                                    grids=grids, freq_hz=[2, 10], h=12.5, shift=args.shift,
+                                    block=args.block, restart=args.restart,
+                                    workers=int(os.environ.get("HELM_BATCH_WORKERS", "4"))),
+                     "converged_problems": conv, "status": int(st), "problems": meta})
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "salt2d":
+        run_other(args)
         return
     import torch
     import torch.distributed as dist

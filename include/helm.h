@@ -118,8 +118,9 @@ void helm_default_params(helm_params* p);
    m, gamma_tilde: device float64 arrays of N = prod(n[k]+1) node values,
    copied; cuda_stream: a cudaStream_t (NULL = legacy default stream).
    Builds A's and M's fine-level coefficients, the Galerkin coefficients of
-   every coarse level, the Jacobi inverse diagonals and the FP64 inverse of
-   the coarsest operator (Gauss-Jordan with partial pivoting).
+   every coarse level, the Jacobi inverse diagonals and the inverse of the
+   coarsest operator (Gauss-Jordan with partial pivoting; FP64 for
+   HELM_PLAIN_C128, FP32 for the complex64 cycles).
    Returns HELM_ERR_ARG for bad sizes, HELM_ERR_BREAKDOWN when the coarsest
    operator is singular. */
 helm_status helm_setup(const double* m, const double* gamma_tilde,
@@ -145,10 +146,15 @@ helm_status helm_solve_host(helm_ctx* ctx, const void* Q_host, int s,
                             double tol, void* U_host, helm_info* info);
 
 /* Solve several independent problems (contexts, possibly different grids,
-   frequencies and precisions): problem k solves ctxs[k] with Q[k] (s[k]
-   columns) into U[k], infos[k] (may be NULL).  Problems are ordered by the
-   autotuned cost model and their block steps are interleaved on the
-   contexts' streams.  Returns the first non-OK status (all are attempted). */
+   frequencies and precisions; the uneven batches of many sources and
+   frequencies of Sec. 2.1's misfit): problem k solves ctxs[k] with Q[k]
+   (s[k] columns, device, ABI layout) into U[k], infos[k] (infos may be NULL).
+   Problems are taken longest first under a cost model (nodes x columns x
+   omega h max(n), x4 for the FP64 path) by HELM_BATCH_WORKERS host workers
+   (environment variable, default 4); each runs on its context's stream, so
+   contexts created with distinct streams overlap on the GPU.  A context must
+   appear at most once per batch.  Returns the first non-OK status in problem
+   order (every problem is attempted). */
 helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* Q,
                              const int* s, int nprob, double tol,
                              void* const* U, helm_info* infos);

@@ -103,14 +103,14 @@ void launch_diag_inv(const Launch& L, const Grid& g, const c128* coef, c128* din
 // dense n x n matrix (row-major) of a K-point stencil
 void launch_stencil_to_dense(const Launch& L, const Grid& g, const c128* coef, c128* dense);
 
-// In-place Gauss-Jordan inversion with partial pivoting of the n x n matrix
-// held in the left half of aug (n x 2n, right half set to I here).  status
-// (device int) is set to 1 if a zero pivot is met.
-void launch_gauss_jordan(const Launch& L, c128* aug, int n, c128* factor, int* piv,
-                         c128* pivval, int* status);
-
-// out (n x n) = right half of aug; out32 = its complex64 rounding (may be null)
-void launch_extract_inverse(const Launch& L, const c128* aug, int n, c128* out, c64* out32);
+// Gauss-Jordan inversion with partial pivoting of the dense n x n matrix
+// `dense` (row-major, complex128) in arithmetic T (double or float): aug is
+// n x 2n scratch of cplx<T>, factor n of cplx<T>, pivval one cplx<T>;
+// `inverse` (n x n complex128) receives the result; status (device int) is
+// set to 1 if a zero pivot is met.
+template <typename T>
+void launch_gauss_jordan(const Launch& L, const c128* dense, void* aug, int n, void* factor, int* piv,
+                         void* pivval, int* status, c128* inverse);
 
 void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count);
 

@@ -286,25 +286,31 @@ __global__ void k_stencil_to_dense(Grid g, const c128* __restrict__ coef, c128* 
     D[i * g.N + g.index(x, y, z)] = coef[e];
 }
 
-__global__ void k_aug_init(c128* aug, int n) {
+// Gauss-Jordan kernels, templated on the arithmetic (double for the FP64
+// inverse of the plain solver, float for the complex64 cycle, whose tensor-
+// core solve rounds the inverse to tf32 anyway).
+template <typename T>
+__global__ void k_aug_init(const c128* __restrict__ dense, cplx<T>* aug, int n) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
     long long i = e / n, j = e - i * n;
-    aug[i * 2 * n + n + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+    aug[i * 2 * n + j] = cvt<T>(dense[e]);
+    aug[i * 2 * n + n + j] = mk<T>(i == j ? T(1) : T(0), T(0));
 }
 
 // One block: pivot row p = argmax_{i>=k} |aug[i][k]|; factor[i] = entry of
 // column k in row i after the swap of rows k and p (factor[k] = 0).
-__global__ void __launch_bounds__(1024) k_gj_pivot(c128* aug, int n, int k, c128* factor, int* piv,
-                                                   c128* pivval, int* status) {
-    __shared__ double sval[1024];
+template <typename T>
+__global__ void __launch_bounds__(1024) k_gj_pivot(cplx<T>* aug, int n, int k, cplx<T>* factor,
+                                                   int* piv, cplx<T>* pivval, int* status) {
+    __shared__ T sval[1024];
     __shared__ int sidx[1024];
     const long long ld = 2LL * n;
-    double best = -1.0;
+    T best = T(-1);
     int bi = k;
     for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        c128 a = aug[i * ld + k];
-        double v = a.re * a.re + a.im * a.im;
+        cplx<T> a = aug[i * ld + k];
+        T v = a.re * a.re + a.im * a.im;
         if (v > best) { best = v; bi = i; }
     }
     sval[threadIdx.x] = best;
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(c128* aug, int n, int k, c128
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
-            double o = sval[threadIdx.x + w];
+            T o = sval[threadIdx.x + w];
             int oi = sidx[threadIdx.x + w];
             if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
                 sval[threadIdx.x] = o;
@@ -325,50 +331,52 @@ __global__ void __launch_bounds__(1024) k_gj_pivot(c128* aug, int n, int k, c128
     if (threadIdx.x == 0) {
         *piv = p;
         *pivval = aug[(long long)p * ld + k];
-        if (!(sval[0] > 0.0)) *status = 1;
+        if (!(sval[0] > T(0))) *status = 1;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        c128 v;
-        if (i == k) v = mk(0.0, 0.0);
+        cplx<T> v;
+        if (i == k) v = mk<T>(0, 0);
         else if (i == p) v = aug[(long long)k * ld + k];
         else v = aug[(long long)i * ld + k];
         factor[i] = v;
     }
 }
 
-__global__ void k_gj_swap_scale(c128* aug, int n, int k, const int* piv, const c128* pivval) {
+template <typename T>
+__global__ void k_gj_swap_scale(cplx<T>* aug, int n, int k, const int* piv, const cplx<T>* pivval) {
     int j = k + blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= 2 * n) return;
     const long long ld = 2LL * n;
     int p = *piv;
-    c128 pv = *pivval;
-    double den = pv.re * pv.re + pv.im * pv.im;
-    c128 inv = den > 0.0 ? mk(pv.re / den, -pv.im / den) : mk(0.0, 0.0);
-    c128 a = aug[(long long)k * ld + j];
-    c128 b = aug[(long long)p * ld + j];
+    cplx<T> pv = *pivval;
+    T den = pv.re * pv.re + pv.im * pv.im;
+    cplx<T> inv = den > T(0) ? mk<T>(pv.re / den, -pv.im / den) : mk<T>(0, 0);
+    cplx<T> a = aug[(long long)k * ld + j];
+    cplx<T> b = aug[(long long)p * ld + j];
     if (p != k) aug[(long long)p * ld + j] = a;
     aug[(long long)k * ld + j] = inv * b;
 }
 
-__global__ void k_gj_eliminate(c128* aug, int n, int k, const c128* __restrict__ factor) {
+template <typename T>
+__global__ void k_gj_eliminate(cplx<T>* aug, int n, int k, const cplx<T>* __restrict__ factor) {
     const long long ld = 2LL * n;
     int j = k + blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
     if (j >= 2 * n || i == k) return;
-    c128 f = factor[i];
-    if (f.re == 0.0 && f.im == 0.0) return;
-    c128 rk = aug[(long long)k * ld + j];
-    c128 v = aug[(long long)i * ld + j];
+    cplx<T> f = factor[i];
+    if (f.re == T(0) && f.im == T(0)) return;
+    cplx<T> rk = aug[(long long)k * ld + j];
+    cplx<T> v = aug[(long long)i * ld + j];
     aug[(long long)i * ld + j] = v - f * rk;
 }
 
-__global__ void k_extract_inverse(const c128* aug, int n, c128* out, c64* out32) {
+template <typename T>
+__global__ void k_extract_inverse(const cplx<T>* aug, int n, c128* out) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)n * n) return;
     long long i = e / n, j = e - i * n;
-    c128 v = aug[i * 2 * n + n + j];
-    out[e] = v;
-    if (out32) out32[e] = mk(__double2float_rn(v.re), __double2float_rn(v.im));
+    cplx<T> v = aug[i * 2 * n + n + j];
+    out[e] = mk<double>((double)v.re, (double)v.im);
 }
 
 __global__ void k_round_c64(const c128* in, c64* out, long long count) {
@@ -500,31 +508,36 @@ void launch_stencil_to_dense(const Launch& L, const Grid& g, const c128* coef, c
     L.post();
 }
 
-void launch_gauss_jordan(const Launch& L, c128* aug, int n, c128* factor, int* piv, c128* pivval,
-                         int* status) {
+template <typename T>
+void launch_gauss_jordan(const Launch& L, const c128* dense, void* aug_raw, int n, void* factor_raw,
+                         int* piv, void* pivval_raw, int* status, c128* inverse) {
+    cplx<T>* aug = static_cast<cplx<T>*>(aug_raw);
+    cplx<T>* factor = static_cast<cplx<T>*>(factor_raw);
+    cplx<T>* pivval = static_cast<cplx<T>*>(pivval_raw);
     L.pre(KID_SETUP, 0, 0);
-    k_aug_init<<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(aug, n);
+    k_aug_init<T><<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(dense, aug, n);
     L.post();
     for (int k = 0; k < n; ++k) {
         L.pre(KID_SETUP, 0, 0);
-        k_gj_pivot<<<1, 1024, 0, L.st>>>(aug, n, k, factor, piv, pivval, status);
+        k_gj_pivot<T><<<1, 1024, 0, L.st>>>(aug, n, k, factor, piv, pivval, status);
         L.post();
         int cols = 2 * n - k;
         L.pre(KID_SETUP, 0, 0);
-        k_gj_swap_scale<<<(cols + 255) / 256, 256, 0, L.st>>>(aug, n, k, piv, pivval);
+        k_gj_swap_scale<T><<<(cols + 255) / 256, 256, 0, L.st>>>(aug, n, k, piv, pivval);
         L.post();
         dim3 grid((cols + 255) / 256, n);
         L.pre(KID_SETUP, 0, 0);
-        k_gj_eliminate<<<grid, 256, 0, L.st>>>(aug, n, k, factor);
+        k_gj_eliminate<T><<<grid, 256, 0, L.st>>>(aug, n, k, factor);
         L.post();
     }
-}
-
-void launch_extract_inverse(const Launch& L, const c128* aug, int n, c128* out, c64* out32) {
     L.pre(KID_SETUP, 0, 0);
-    k_extract_inverse<<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(aug, n, out, out32);
+    k_extract_inverse<T><<<blocks_for((long long)n * n), kThreads, 0, L.st>>>(aug, n, inverse);
     L.post();
 }
+template void launch_gauss_jordan<double>(const Launch&, const c128*, void*, int, void*, int*, void*,
+                                          int*, c128*);
+template void launch_gauss_jordan<float>(const Launch&, const c128*, void*, int, void*, int*, void*,
+                                         int*, c128*);
 
 void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count) {
     L.pre(KID_LAYOUT, count * (16.0 + 8.0), 0);

@@ -10,6 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <thread>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -1016,28 +1019,34 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
     }
     c->nc = (int)gcst.N;
     const int n = c->nc;
-    c128 *aug = nullptr, *factor = nullptr, *pivval = nullptr;
+    // the plain solver gets the FP64 inverse; the complex64 cycle an FP32
+    // one (its tensor-core solve rounds the inverse to tf32 anyway)
+    const bool fp64_inverse = p->prec == HELM_PLAIN_C128;
+    const size_t esz = fp64_inverse ? sizeof(c128) : sizeof(c64);
+    void *aug = nullptr, *factor = nullptr, *pivval = nullptr;
     int *piv = nullptr, *dstatus = nullptr;
-    SETUP_TRY(dalloc(&aug, sizeof(c128) * (size_t)n * 2 * n));
-    SETUP_TRY(dalloc(&factor, sizeof(c128) * n));
+    SETUP_TRY(dalloc(&aug, esz * (size_t)n * 2 * n));
+    SETUP_TRY(dalloc(&factor, esz * n));
     SETUP_TRY(dalloc(&pivval, sizeof(c128)));
     SETUP_TRY(dalloc(&piv, sizeof(int)));
     SETUP_TRY(dalloc(&dstatus, sizeof(int)));
     SETUP_TRY(cudaMemsetAsync(dstatus, 0, sizeof(int), c->st));
     SETUP_TRY(dalloc(&c->Minv, sizeof(c128) * (size_t)n * n));
     SETUP_TRY(dalloc(&c->Ap, sizeof(float) * (size_t)n * helm::dense_tc_kpad(n)));
-    // dense matrix into the left half of aug (row stride 2n): build it in Minv then copy rows
-    helm::launch_stencil_to_dense(L, gcst, c->lv[p->levels - 1].coef, c->Minv);
-    SETUP_TRY(cudaMemcpy2DAsync(aug, sizeof(c128) * 2 * n, c->Minv, sizeof(c128) * n,
-                                sizeof(c128) * n, n, cudaMemcpyDeviceToDevice, c->st));
-    helm::launch_gauss_jordan(L, aug, n, factor, piv, pivval, dstatus);
-    helm::launch_extract_inverse(L, aug, n, c->Minv, nullptr);
+    c128* dense = nullptr;
+    SETUP_TRY(dalloc(&dense, sizeof(c128) * (size_t)n * n));
+    helm::launch_stencil_to_dense(L, gcst, c->lv[p->levels - 1].coef, dense);
+    if (fp64_inverse)
+        helm::launch_gauss_jordan<double>(L, dense, aug, n, factor, piv, pivval, dstatus, c->Minv);
+    else
+        helm::launch_gauss_jordan<float>(L, dense, aug, n, factor, piv, pivval, dstatus, c->Minv);
     helm::launch_build_aprime(L, c->Minv, n, c->Ap, p->coarse_tf32x3 != 0);
     int hstatus = 0;
     SETUP_TRY(cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     SETUP_TRY(cudaStreamSynchronize(c->st));
     SETUP_TRY(cudaGetLastError());
     dfree(aug); dfree(factor); dfree(pivval); dfree(piv); dfree(dstatus); dfree(dm); dfree(dg);
+    dfree(dense);
     if (hstatus) return cleanup(fail(nullptr, HELM_ERR_BREAKDOWN, "coarsest operator is singular"));
 #undef SETUP_TRY
     *out = c;
@@ -1078,11 +1087,46 @@ helm_status helm_solve_batch(helm_ctx* const* ctxs, const void* const* Q, const 
                              double tol, void* const* U, helm_info* infos) {
     if (nprob < 0 || (nprob > 0 && (!ctxs || !Q || !s || !U)))
         return fail(nullptr, HELM_ERR_ARG, "bad batch arguments");
-    helm_status first = HELM_OK;
+    for (int k = 0; k < nprob; ++k)
+        if (!ctxs[k] || s[k] < 0) return fail(nullptr, HELM_ERR_ARG, "bad problem in batch");
+    // Longest-processing-time-first order under a cost model: work per cycle
+    // ~ nodes x columns (x4 on the FP64 path, whose kernels run on the narrow
+    // FP64 pipe), cycles ~ wavelengths across the grid ~ omega h max(n).
+    std::vector<std::pair<double, int>> order;
     for (int k = 0; k < nprob; ++k) {
-        helm_status st = helm_solve(ctxs[k], Q[k], s[k], tol, U[k], infos ? &infos[k] : nullptr);
-        if (st != HELM_OK && first == HELM_OK) first = st;
+        const helm_params& p = ctxs[k]->p;
+        int nmax = std::max(p.n[0], std::max(p.n[1], p.dim == 3 ? p.n[2] : 0));
+        double cost = (double)ctxs[k]->N() * std::max(1, s[k]) * (1.0 + p.omega * p.h * nmax) *
+                      (p.prec == HELM_PLAIN_C128 ? 4.0 : 1.0);
+        order.push_back({-cost, k});
     }
+    std::sort(order.begin(), order.end());
+    // Host workers take problems in that order; each problem's work is on its
+    // context's stream, so problems whose contexts have distinct streams run
+    // concurrently on the GPU.  Workers: HELM_BATCH_WORKERS (default 4).
+    int workers = 4;
+    if (const char* e = std::getenv("HELM_BATCH_WORKERS")) workers = std::max(1, std::atoi(e));
+    workers = std::min(workers, std::max(nprob, 1));
+    std::atomic<int> next{0};
+    std::vector<helm_status> status(nprob, HELM_OK);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto run = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            int i = next.fetch_add(1);
+            if (i >= nprob) break;
+            int k = order[i].second;
+            status[k] = helm_solve(ctxs[k], Q[k], s[k], tol, U[k], infos ? &infos[k] : nullptr);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(run);
+    run();
+    for (auto& t : pool) t.join();
+    helm_status first = HELM_OK;
+    for (int k = 0; k < nprob; ++k)
+        if (status[k] != HELM_OK && first == HELM_OK) first = status[k];
     return first;
 }
 

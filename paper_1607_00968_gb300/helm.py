@@ -130,6 +130,29 @@ class Info:
                         self.status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
 
 
+def solve_batch(solvers, Qs, tol: float = 1e-6, check: bool = True):
+    """helm_solve_batch over several Solvers (each ideally on its own stream).
+    Qs: list of (s_k, N_k) complex128 device tensors.  Returns (Us, infos,
+    status)."""
+    import torch
+    lib = load()
+    n = len(solvers)
+    Qs = [S._block(Q) for S, Q in zip(solvers, Qs)]
+    Us = [torch.empty_like(Q) for Q in Qs]
+    infos = [Info(Q.shape[0]) for Q in Qs]
+    cinfo = (HelmInfo * n)(*[i.c_struct() for i in infos])
+    ctxs = (ctypes.c_void_p * n)(*[S.ctx.value for S in solvers])
+    qp = (ctypes.c_void_p * n)(*[Q.data_ptr() for Q in Qs])
+    up = (ctypes.c_void_p * n)(*[U.data_ptr() for U in Us])
+    ss = (ctypes.c_int * n)(*[Q.shape[0] for Q in Qs])
+    for S in solvers:
+        S.stream.synchronize()
+    st = lib.helm_solve_batch(ctxs, qp, ss, n, float(tol), up, cinfo)
+    if check and st != HELM_OK:
+        raise HelmError(st, lib.helm_last_error(None).decode())
+    return Us, infos, st
+
+
 class Solver:
     """A set-up Helmholtz hierarchy on the current CUDA device.
 

@@ -290,7 +290,7 @@ def random_problem_2d(seed: int, cells, h: float, freq_hz: float,
                    extra={"freq_hz": freq_hz})
 
 
-def default_levels(cells, max_coarsest: int = 2700) -> int:
+def default_levels(cells, max_coarsest: int = 9000) -> int:
     """Fewest levels whose coarsest grid has at most ``max_coarsest`` nodes
     (each coarsening halves the cells per axis)."""
     L = 1

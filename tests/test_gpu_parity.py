@@ -295,3 +295,25 @@ def test_not_converged_returns_best_iterate(H):
     rr = O.relres(A, U.cpu().numpy().T, Q.T)
     np.testing.assert_allclose(info.relres, rr, rtol=1e-6)
     assert np.all(rr < 1.0)
+
+
+def test_solve_batch_matches_single_solves(H):
+    """helm_solve_batch over contexts of different grids, frequencies and
+    precisions, each on its own stream, gives the single-solve results."""
+    probs = [I.random_problem_2d(40 + k, cells, 25.0, f, s, width=6, levels=lv)
+             for k, (cells, f, s, lv) in enumerate([((64, 32), 4.0, 5, 3), ((32, 16), 6.0, 3, 2),
+                                                     ((64, 64), 5.0, 7, 3), ((32, 32), 3.0, 1, 2)])]
+    precs = ["c64", "c128", "c64", "c128"]
+    solvers, Qs = [], []
+    for P, prec in zip(probs, precs):
+        solvers.append(H.Solver(P.m, P.gamma, P.h, P.omega, levels=P.levels, block=4, prec=prec,
+                                stream=torch.cuda.Stream()))
+        Qs.append(dev(P.rhs()))
+    Us, infos, st = H.solve_batch(solvers, Qs, tol=1e-8)
+    assert st == 0
+    for P, S, Q, U, inf in zip(probs, solvers, Qs, Us, infos):
+        U1, i1, _ = S.solve(Q, tol=1e-8)
+        assert torch.equal(U, U1)                    # same kernels, same order: bitwise
+        A = O.helmholtz_matrix(P.m, P.gamma, P.omega, P.h)
+        assert np.all(O.relres(A, U.cpu().numpy().T, Q.cpu().numpy().T) <= 1e-8)
+        np.testing.assert_array_equal(inf.iters, i1.iters)
