@@ -114,6 +114,36 @@ __device__ __forceinline__ cplx<T> ldg(const cplx<T>* p) {
     return z;
 }
 
+// R consecutive complex values (R = 1 or 2) loaded/stored with one vector
+// access where the type allows it (the pair is 16-byte aligned when the first
+// column index is even).
+template <typename T, int R>
+struct CV {
+    cplx<T> v[R];
+};
+template <typename U, int R>
+__device__ __forceinline__ CV<U, R> ldR(const cplx<U>* p) {
+    CV<U, R> o;
+    if constexpr (R == 2 && sizeof(U) == 4) {
+        float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        o.v[0] = mk<U>(q.x, q.y);
+        o.v[1] = mk<U>(q.z, q.w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) o.v[k] = ldg(p + k);
+    }
+    return o;
+}
+template <typename U, int R>
+__device__ __forceinline__ void stR(cplx<U>* p, const CV<U, R>& o) {
+    if constexpr (R == 2 && sizeof(U) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(o.v[0].re, o.v[0].im, o.v[1].re, o.v[1].im);
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) p[k] = o.v[k];
+    }
+}
+
 // Grid of nodes; x1 fastest.  n[2] = 1 in 2D.
 struct Grid {
     int dim;
@@ -161,6 +191,39 @@ struct FineOp {
         return y_ - ci * ui;
     }
     __device__ __forceinline__ cplx<T> diag_inv(long long node) const { return ldg(dinv + node); }
+
+    // the same for R consecutive columns r0 .. r0+R-1
+    template <int R, typename U>
+    __device__ __forceinline__ void applyR(const cplx<U>* u, long long node, int x, int y, int z,
+                                           int s, int r0, cplx<T>* out) const {
+        const cplx<U>* p = u + node * s + r0;
+        CV<U, R> ui = ldR<U, R>(p);
+        cplx<T> sum[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) sum[k] = mk<T>(0, 0);
+        auto add = [&](const cplx<U>* q) {
+            CV<U, R> v = ldR<U, R>(q);
+#pragma unroll
+            for (int k = 0; k < R; ++k) sum[k] = sum[k] + cvt<T>(v.v[k]);
+        };
+        if (x > 0) add(p - s);
+        if (x < g.n1 - 1) add(p + s);
+        const long long sy = (long long)g.n1 * s;
+        if (y > 0) add(p - sy);
+        if (y < g.n2 - 1) add(p + sy);
+        if (g.dim == 3) {
+            const long long sz = (long long)g.n1 * g.n2 * s;
+            if (z > 0) add(p - sz);
+            if (z < g.n3 - 1) add(p + sz);
+        }
+        const T dd = (T)(2 * g.dim);
+        const cplx<T> ci = ldg(c + node);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            cplx<T> uk = cvt<T>(ui.v[k]);
+            out[k] = inv_h2 * mk<T>(dd * uk.re - sum[k].re, dd * uk.im - sum[k].im) - ci * uk;
+        }
+    }
 };
 
 // Galerkin coarse operator: 9-point (2D) or 27-point (3D) stencil with
@@ -197,6 +260,34 @@ struct GalOp {
         return acc;
     }
     __device__ __forceinline__ cplx<T> diag_inv(long long node) const { return ldg(dinv + node); }
+
+    // the same for R consecutive columns r0 .. r0+R-1
+    template <int R, typename U>
+    __device__ __forceinline__ void applyR(const cplx<U>* u, long long node, int x, int y, int z,
+                                           int s, int r0, cplx<T>* out) const {
+        const int K = g.dim == 3 ? 27 : 9;
+        const cplx<T>* cf = coef + node * K;
+#pragma unroll
+        for (int k = 0; k < R; ++k) out[k] = mk<T>(0, 0);
+        const int z0 = g.dim == 3 ? -1 : 0, z1 = g.dim == 3 ? 1 : 0;
+        for (int dz = z0; dz <= z1; ++dz) {
+            int zz = z + dz;
+            if (zz < 0 || zz >= g.n3) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = y + dy;
+                if (yy < 0 || yy >= g.n2) continue;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = x + dx;
+                    if (xx < 0 || xx >= g.n1) continue;
+                    int o = (dx + 1) + 3 * (dy + 1) + (g.dim == 3 ? 9 * (dz + 1) : 0);
+                    cplx<T> cc = ldg(cf + o);
+                    CV<U, R> uv = ldR<U, R>(u + g.index(xx, yy, zz) * s + r0);
+#pragma unroll
+                    for (int k = 0; k < R; ++k) fma_acc(out[k], cc, cvt<T>(uv.v[k]));
+                }
+            }
+        }
+    }
 };
 
 // Kernel classes seen by the profiler (helm_profile_* in helm.h).

@@ -146,6 +146,143 @@ __global__ void __launch_bounds__(kThreads) k_prolong_add(Grid gf, Grid gc,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Division-free variants: block (TX, TY) covers TY consecutive nodes of one
+// grid row (blockIdx.y = x2 index, blockIdx.z = x3 index) and TX * R columns;
+// thread (tx, ty) owns columns tx*R .. tx*R+R-1 of node x = blockIdx.x*TY + ty.
+// R = 2 when s is even (one 16-byte access per complex64 pair).
+// ---------------------------------------------------------------------------
+
+struct Geo {
+    dim3 grid, block;
+    int R;
+    bool ok;
+};
+
+inline Geo geo_for(const Grid& g, int s) {
+    Geo o;
+    o.R = (s % 2 == 0) ? 2 : 1;
+    int tx = s / o.R;
+    o.ok = tx <= 256;
+    int ty = tx >= 256 ? 1 : 256 / tx;
+    o.block = dim3(tx, ty, 1);
+    o.grid = dim3((g.n1 + ty - 1) / ty, g.n2, g.n3);
+    return o;
+}
+
+#define VGEO_PROLOGUE(G)                                                   \
+    const int x = blockIdx.x * blockDim.y + threadIdx.y;                   \
+    if (x >= (G).n1) return;                                               \
+    const int y = blockIdx.y, z = blockIdx.z;                              \
+    const long long node = ((long long)z * (G).n2 + y) * (G).n1 + x;       \
+    const int r0 = threadIdx.x * R;                                        \
+    const long long e0 = node * s + r0;
+
+template <typename T, typename U, typename V, typename Op, int R>
+__global__ void __launch_bounds__(256) k_apply_v(Op op, const cplx<U>* __restrict__ xin,
+                                                  cplx<V>* __restrict__ yout, int s) {
+    VGEO_PROLOGUE(op.g)
+    cplx<T> o[R];
+    op.template applyR<R>(xin, node, x, y, z, s, r0, o);
+    CV<V, R> w;
+#pragma unroll
+    for (int k = 0; k < R; ++k) w.v[k] = cvt<V>(o[k]);
+    stR<V, R>(yout + e0, w);
+}
+
+template <typename T, typename FT, typename Op, int R>
+__global__ void __launch_bounds__(256) k_jacobi_v(Op op, const cplx<T>* __restrict__ uin,
+                                                   const cplx<FT>* __restrict__ f,
+                                                   cplx<T>* __restrict__ uout, int s, T w) {
+    VGEO_PROLOGUE(op.g)
+    CV<FT, R> fv = ldR<FT, R>(f + e0);
+    const cplx<T> d = op.diag_inv(node);
+    CV<T, R> outv;
+    if (uin == nullptr) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) outv.v[k] = w * (d * cvt<T>(fv.v[k]));
+    } else {
+        cplx<T> Au[R];
+        op.template applyR<R>(uin, node, x, y, z, s, r0, Au);
+        CV<T, R> ui = ldR<T, R>(uin + e0);
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            outv.v[k] = ui.v[k] + w * (d * (cvt<T>(fv.v[k]) - Au[k]));
+    }
+    stR<T, R>(uout + e0, outv);
+}
+
+// coarse node J = (x, y, z) on gc; gathers the 3^d fine nodes 2J + delta
+template <typename T, typename FT, typename Op, int R>
+__global__ void __launch_bounds__(256) k_resid_restrict_v(Op op, Grid gc, const cplx<T>* __restrict__ u,
+                                                           const cplx<FT>* __restrict__ f,
+                                                           cplx<T>* __restrict__ rc, int s) {
+    VGEO_PROLOGUE(gc)
+    const Grid& gf = op.g;
+    cplx<T> acc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = mk<T>(0, 0);
+    const int z0 = gf.dim == 3 ? -1 : 0, z1 = gf.dim == 3 ? 1 : 0;
+    for (int dz = z0; dz <= z1; ++dz) {
+        int fz = gf.dim == 3 ? 2 * z + dz : 0;
+        if (fz < 0 || fz >= gf.n3) continue;
+        T wz = dz == 0 ? T(1) : T(0.5);
+        for (int dy = -1; dy <= 1; ++dy) {
+            int fy = 2 * y + dy;
+            if (fy < 0 || fy >= gf.n2) continue;
+            T wy = dy == 0 ? wz : T(0.5) * wz;
+            for (int dx = -1; dx <= 1; ++dx) {
+                int fx = 2 * x + dx;
+                if (fx < 0 || fx >= gf.n1) continue;
+                T wgt = dx == 0 ? wy : T(0.5) * wy;
+                long long i = gf.index(fx, fy, fz);
+                CV<FT, R> fv = ldR<FT, R>(f + i * s + r0);
+                cplx<T> Au[R];
+                if (u != nullptr) op.template applyR<R>(u, i, fx, fy, fz, s, r0, Au);
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    cplx<T> ri = cvt<T>(fv.v[k]);
+                    if (u != nullptr) ri = ri - Au[k];
+                    acc[k] = acc[k] + wgt * ri;
+                }
+            }
+        }
+    }
+    CV<T, R> o;
+#pragma unroll
+    for (int k = 0; k < R; ++k) o.v[k] = acc[k];
+    stR<T, R>(rc + e0, o);
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_prolong_add_v(Grid gf, Grid gc, const cplx<T>* __restrict__ ec,
+                                                        cplx<T>* __restrict__ u, int s) {
+    VGEO_PROLOGUE(gf)
+    int xs[2], ys[2], zs[2];
+    int nx = (x & 1) ? 2 : 1, ny = (y & 1) ? 2 : 1, nz = (gf.dim == 3 && (z & 1)) ? 2 : 1;
+    xs[0] = x >> 1; xs[1] = (x >> 1) + 1;
+    ys[0] = y >> 1; ys[1] = (y >> 1) + 1;
+    zs[0] = z >> 1; zs[1] = (z >> 1) + 1;
+    T wgt = T(1);
+    if (nx == 2) wgt *= T(0.5);
+    if (ny == 2) wgt *= T(0.5);
+    if (nz == 2) wgt *= T(0.5);
+    cplx<T> acc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = mk<T>(0, 0);
+    for (int c = 0; c < nz; ++c)
+        for (int b = 0; b < ny; ++b)
+            for (int a = 0; a < nx; ++a) {
+                CV<T, R> v = ldR<T, R>(ec + gc.index(xs[a], ys[b], zs[c]) * s + r0);
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[k] = acc[k] + v.v[k];
+            }
+    CV<T, R> uv = ldR<T, R>(u + e0);
+#pragma unroll
+    for (int k = 0; k < R; ++k) uv.v[k] = uv.v[k] + wgt * acc[k];
+    stR<T, R>(u + e0, uv);
+}
+
 // u = Minv f: tiled complex GEMM (n x n) * (n x s), 32 x 32 output tile per
 // block, 16-deep k tiles staged in shared memory, 4 outputs per thread.
 template <typename T>
@@ -414,7 +551,10 @@ void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, i
     L.pre(OpCost<Op>::fine ? KID_APPLY_FINE : KID_APPLY_COARSE,
           total * (cb<U>() + cb<V>()) + op.g.N * OpCost<Op>::coef_bytes(op),
           total * OpCost<Op>::flops(op));
-    k_apply<T, U, V, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, x, y, s, total);
+    Geo G = geo_for(op.g, s);
+    if (G.ok && G.R == 2) k_apply_v<T, U, V, Op, 2><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
+    else if (G.ok) k_apply_v<T, U, V, Op, 1><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
+    else k_apply<T, U, V, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, x, y, s, total);
     L.post();
 }
 
@@ -441,7 +581,10 @@ void launch_jacobi(const Launch& L, const Op& op, const cplx<T>* u_in, const cpl
         flops = total * (OpCost<Op>::flops(op) + 12.0);
     }
     L.pre(OpCost<Op>::fine ? KID_JACOBI_FINE : KID_JACOBI_COARSE, bytes, flops);
-    k_jacobi<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, u_in, f, u_out, s, w, total);
+    Geo G = geo_for(op.g, s);
+    if (G.ok && G.R == 2) k_jacobi_v<T, FT, Op, 2><<<G.grid, G.block, 0, L.st>>>(op, u_in, f, u_out, s, w);
+    else if (G.ok) k_jacobi_v<T, FT, Op, 1><<<G.grid, G.block, 0, L.st>>>(op, u_in, f, u_out, s, w);
+    else k_jacobi<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, u_in, f, u_out, s, w, total);
     L.post();
 }
 
@@ -454,7 +597,13 @@ void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const 
                    op.g.N * OpCost<Op>::coef_bytes(op);
     double flops = ef * ((u ? OpCost<Op>::flops(op) : 0.0) + 2.0) + total * 2.0 * (op.g.dim == 3 ? 27 : 9);
     L.pre(OpCost<Op>::fine ? KID_RESTRICT_FINE : KID_RESTRICT_COARSE, bytes, flops);
-    k_resid_restrict<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, gc, u, f, rc, s, total);
+    Geo G = geo_for(gc, s);
+    if (G.ok && G.R == 2)
+        k_resid_restrict_v<T, FT, Op, 2><<<G.grid, G.block, 0, L.st>>>(op, gc, u, f, rc, s);
+    else if (G.ok)
+        k_resid_restrict_v<T, FT, Op, 1><<<G.grid, G.block, 0, L.st>>>(op, gc, u, f, rc, s);
+    else
+        k_resid_restrict<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, gc, u, f, rc, s, total);
     L.post();
 }
 
@@ -464,7 +613,10 @@ void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const c
     long long total = gf.N * s;
     L.pre(KID_PROLONG, total * 2 * cb<T>() + (double)gc.N * s * cb<T>(),
           total * 2.0 * (gf.dim == 3 ? 8 : 4));
-    k_prolong_add<T><<<blocks_for(total), kThreads, 0, L.st>>>(gf, gc, ec, u, s, total);
+    Geo G = geo_for(gf, s);
+    if (G.ok && G.R == 2) k_prolong_add_v<T, 2><<<G.grid, G.block, 0, L.st>>>(gf, gc, ec, u, s);
+    else if (G.ok) k_prolong_add_v<T, 1><<<G.grid, G.block, 0, L.st>>>(gf, gc, ec, u, s);
+    else k_prolong_add<T><<<blocks_for(total), kThreads, 0, L.st>>>(gf, gc, ec, u, s, total);
     L.post();
 }
 
