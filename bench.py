@@ -478,6 +478,22 @@ def main():
         for S in ps:
             S.close()
 
+    # ---------------- the paper's fastest variant beside it: W-BiCG ----------------
+    wbicg = None
+    if not args.no_plain:
+        ws = [helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, block=1,
+                          prec="c64", cycle="W", krylov="bicgstab", restart=50, max_restarts=5,
+                          levels=args.levels, **SOLVER) for P in probs]
+        for S in ws:
+            S.solve(Qd, TOL)
+        wms, winfos = timed_steps(torch, ws, Qd, 1, stream)
+        wbicg = {"value": NSRC * len(FREQS_HZ) / (wms / 1e3), "unit": UNIT, "ms_per_step": wms,
+                 "cycles": [int(np.max(i.iters)) for i in winfos],
+                 "what": "BiCGSTAB + W-cycles (Sec. 5.3 W-BiCG), block 1 (64 lock-step groups), "
+                         "complex64 cycle, FP64-class Krylov"}
+        for S in ws:
+            S.close()
+
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -508,7 +524,7 @@ def main():
                              ((args.restart + 1) * Q.nbytes / 1e9),
                        "parallelism": "dp%d (independent models per rank)" % world},
             "cycles_per_frequency": iters, "max_relres": relres,
-            "roofline": roof, "kernels": kernels, "plain": plain,
+            "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg,
             "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,

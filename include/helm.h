@@ -98,6 +98,17 @@ typedef struct {
                                 0 = one tf32 product (~1e-3 relative),
                                 1 = three tf32 products on hi/lo splits
                                 (FP32-class)                                    */
+    int cycle_gamma;         /* 1 = V-cycle, 2 = W-cycle (two coarse visits per
+                                level, Sec. 4)                                  */
+    int krylov;              /* 0 = block FGMRES(restart); 1 = block BiCGSTAB
+                                (Sec. 5.3 "W-BiCG", El Guennouni et al.; needs
+                                a fixed preconditioner: not with the learned
+                                stage, and with the complex64 cycle only for
+                                block <= 2 -- measured: larger blocks diverge
+                                under the cycle's FP32 rounding, while the
+                                complex128 cycle converges at any block);
+                                iterations capped at restart * max_restarts
+                                per run, max_restarts + 1 runs                  */
 } helm_params;
 
 typedef struct {
@@ -110,7 +121,7 @@ typedef struct {
 
 /* Fill p with the defaults of Sec. 5.3 (levels 3, V(2,2), weight 0.8,
    restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128,
-   coarse_tf32x3 0. */
+   coarse_tf32x3 0, cycle_gamma 1, krylov 0. */
 void helm_default_params(helm_params* p);
 
 /* Set up the hierarchy for one (m, gamma, omega) (Sec. 4: set-up once, reused

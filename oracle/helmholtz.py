@@ -360,6 +360,112 @@ def block_fgmres(Amat, precond, B: np.ndarray, tol: float = 1e-6,
 
 
 # --------------------------------------------------------------------------
+# Block BiCGSTAB (Sec. 5.3 "W-BiCG": block BiCGSTAB of El Guennouni et al.
+# with a stationary W-cycle preconditioner)
+# --------------------------------------------------------------------------
+
+
+def _small_solve(G, Rhs, rel=1e-14):
+    """Solve G Y = Rhs (s x s, s x s) by Gaussian elimination with partial
+    pivoting; a pivot below rel * max|G| makes its row of Y zero (the block
+    direction it stands for has collapsed)."""
+    n = G.shape[0]
+    Ga = np.array(G, dtype=np.complex128)
+    Y = np.array(Rhs, dtype=np.complex128)
+    scale = np.abs(Ga).max() if Ga.size else 0.0
+    perm = np.arange(n)
+    dead = np.zeros(n, dtype=bool)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(Ga[k:, k])))
+        if p != k:
+            Ga[[k, p]] = Ga[[p, k]]
+            Y[[k, p]] = Y[[p, k]]
+        if abs(Ga[k, k]) <= rel * scale:
+            dead[k] = True
+            continue
+        f = Ga[k + 1:, k] / Ga[k, k]
+        Ga[k + 1:, k:] -= np.outer(f, Ga[k, k:])
+        Y[k + 1:] -= np.outer(f, Y[k])
+    for k in range(n - 1, -1, -1):
+        if dead[k]:
+            Y[k] = 0
+            continue
+        Y[k] = (Y[k] - Ga[k, k + 1:] @ Y[k + 1:]) / Ga[k, k]
+    return Y
+
+
+class BiCGInfo(FGMRESInfo):
+    def __init__(self, s):
+        super().__init__(s)
+        self.biortho = []    # per iteration: max |Rt^H S| / (|Rt| |S|)
+
+
+def block_bicgstab(Amat, precond, B: np.ndarray, tol: float = 1e-6, maxit: int = 500,
+                   max_restarts: int = 5):
+    """Block BiCGSTAB, right-preconditioned, X_0 = 0, shadow block Rt = R_0:
+
+        P_0 = R_0;  for k:  Ph = M P_k, V = A Ph,  alpha = (Rt^H V)^{-1} Rt^H R_k,
+                            S = R_k - V alpha,  Sh = M S,  T = A Sh,
+                            omega = <T, S>_F / <T, T>_F,
+                            X += Ph alpha + omega Sh,  R_{k+1} = S - omega T,
+                            beta = -(Rt^H V)^{-1} Rt^H T,  P_{k+1} = R_{k+1} + (P_k - omega V) beta
+
+    (<X, Y>_F = trace(X^H Y)).  Stops when every column's recursive residual
+    is <= tol ||b_i||, then checks the true residual and restarts from it if
+    needed.  The preconditioner must be fixed and linear (Sec. 5.3: W-BiCG
+    uses W-cycles).  ``iters`` counts preconditioner applications (two per
+    iteration)."""
+    B = np.asarray(B, dtype=np.complex128)
+    N, s = B.shape
+    info = BiCGInfo(s)
+    X = np.zeros_like(B)
+    bnorm = np.linalg.norm(B, axis=0)
+    live = np.nonzero(bnorm > 0)[0]
+    if live.size == 0:
+        info.converged = True
+        return X, info
+    Bl, bl = B[:, live], bnorm[live]
+    Xl = np.zeros_like(Bl)
+    for restart in range(max_restarts + 1):
+        R = Bl - apply(Amat, Xl)
+        rel = np.linalg.norm(R, axis=0) / bl
+        if np.all(rel <= tol) or restart == max_restarts:
+            break
+        info.restarts = restart
+        Rt = R.copy()
+        P = R.copy()
+        for k in range(maxit):
+            Ph = precond(P)
+            V = apply(Amat, Ph)
+            G = Rt.conj().T @ V
+            alpha = _small_solve(G, Rt.conj().T @ R)
+            S = R - V @ alpha
+            nS = np.linalg.norm(S)
+            if nS > 0:
+                info.biortho.append(np.abs(Rt.conj().T @ S).max()
+                                    / (np.linalg.norm(Rt) * nS))
+            Sh = precond(S)
+            T = apply(Amat, Sh)
+            tt = np.vdot(T, T)
+            omega = np.vdot(T, S) / tt if tt != 0 else 0.0
+            Xl = Xl + Ph @ alpha + omega * Sh
+            R = S - omega * T
+            info.iters += 2
+            est = np.linalg.norm(R, axis=0) / bl
+            info.history.append(est)
+            if np.all(est <= tol):
+                break
+            beta = _small_solve(G, -(Rt.conj().T @ T))
+            P = R + (P - omega * V) @ beta
+    R = Bl - apply(Amat, Xl)
+    rel = np.linalg.norm(R, axis=0) / bl
+    info.relres[live] = rel
+    info.converged = bool(np.all(rel <= tol))
+    X[:, live] = Xl
+    return X, info
+
+
+# --------------------------------------------------------------------------
 # Whole solve (the method end to end)
 # --------------------------------------------------------------------------
 
@@ -377,8 +483,22 @@ class Solver:
         self.H = Hierarchy(self.M, self.shape, levels)
         self.pre, self.post, self.w = pre, post, w
 
-    def precond(self, V):
-        return vcycle(self.H, V, 0, self.pre, self.post, self.w)
+    def precond(self, V, gamma: int = 1):
+        return vcycle(self.H, V, 0, self.pre, self.post, self.w, gamma)
+
+    def solve_bicgstab(self, Q_cols: np.ndarray, tol=1e-6, block=None, gamma: int = 2,
+                       maxit=500):
+        """Block BiCGSTAB with W-cycles (gamma = 2) in groups of ``block``."""
+        N, s = Q_cols.shape
+        block = s if block is None else block
+        U = np.zeros_like(Q_cols, dtype=np.complex128)
+        infos = []
+        for g0 in range(0, s, block):
+            sl = slice(g0, min(s, g0 + block))
+            U[:, sl], inf = block_bicgstab(self.A, lambda V: self.precond(V, gamma),
+                                           Q_cols[:, sl], tol, maxit)
+            infos.append(inf)
+        return U, infos
 
     def solve(self, Q_cols: np.ndarray, tol=1e-6, restart=10, block=None,
               max_restarts=50):

@@ -26,6 +26,10 @@ template <typename T, typename FT, typename Op>
 void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const cplx<T>* u,
                            const cplx<FT>* f, cplx<T>* rc, int s);
 
+// y += x (n complex values)
+template <typename T>
+void launch_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, long long n);
+
 // u += P ec
 template <typename T>
 void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const cplx<T>* ec,

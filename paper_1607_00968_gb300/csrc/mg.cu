@@ -523,6 +523,12 @@ __global__ void k_round_c64(const c128* in, c64* out, long long count) {
 
 }  // namespace
 
+template <typename T>
+__global__ void k_axpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, long long n) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < n) y[e] = y[e] + ldg(x + e);
+}
+
 // ---------------- launchers ----------------
 //
 // Each launcher reports the launch's algorithmic traffic and flops to the
@@ -604,6 +610,13 @@ void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const 
         k_resid_restrict_v<T, FT, Op, 1><<<G.grid, G.block, 0, L.st>>>(op, gc, u, f, rc, s);
     else
         k_resid_restrict<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, gc, u, f, rc, s, total);
+    L.post();
+}
+
+template <typename T>
+void launch_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, long long n) {
+    L.pre(KID_PROLONG, n * 3.0 * cb<T>(), n * 2.0);
+    k_axpy<T><<<blocks_for(n), kThreads, 0, L.st>>>(y, x, n);
     L.post();
 }
 
@@ -719,6 +732,9 @@ void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count
                                                         const cplx<T>*, cplx<T>*, int);          \
     template void launch_prolong_add<T>(const Launch&, const Grid&, const Grid&, const cplx<T>*, \
                                         cplx<T>*, int);                                          \
+    template void launch_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, long long);            \
+    template void launch_residual<T, GalOp<T>>(const Launch&, const GalOp<T>&, const cplx<T>*,   \
+                                               const cplx<T>*, cplx<T>*, int);                   \
     template void launch_dense_apply<T>(const Launch&, const cplx<T>*, int, const cplx<T>*,      \
                                         cplx<T>*, int);
 

@@ -53,6 +53,8 @@ struct Level {
     void* u1 = nullptr;
     void* e = nullptr;       // coarse-level solution (levels >= 1)
     void* f = nullptr;       // coarse-level right-hand side (levels >= 1)
+    void* wf = nullptr;      // W-cycle: residual and correction of the second
+    void* we = nullptr;      // coarse visit (levels >= 1)
 };
 
 }  // namespace
@@ -287,6 +289,15 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
     cplx<T>* ec = reinterpret_cast<cplx<T>*>(nxt.e);
     restrict_level<T, FT>(c, l, cur, f, fc, s);
     cycle<T, T>(c, l + 1, fc, ec, s);
+    if (c->p.cycle_gamma == 2 && l + 1 < Lv - 1) {
+        // W-cycle (Sec. 4: two recursive calls): a second coarse visit on the
+        // residual of the first, ec += cycle(fc - M_{l+1} ec)
+        cplx<T>* wf = reinterpret_cast<cplx<T>*>(nxt.wf);
+        cplx<T>* we = reinterpret_cast<cplx<T>*>(nxt.we);
+        helm::launch_residual<T, helm::GalOp<T>>(c->L(), gal_op<T>(c, l + 1), ec, fc, wf, s);
+        cycle<T, T>(c, l + 1, wf, we, s);
+        helm::launch_axpy<T>(c->L(), ec, we, nxt.g.N * (long long)s);
+    }
     cplx<T>* u = const_cast<cplx<T>*>(cur);
     if (u == nullptr) {
         u = bufA;
@@ -311,8 +322,8 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
 
 void free_workspace(helm_ctx* c) {
     for (auto& l : c->lv) {
-        dfree(l.u0); dfree(l.u1); dfree(l.e); dfree(l.f);
-        l.u0 = l.u1 = l.e = l.f = nullptr;
+        dfree(l.u0); dfree(l.u1); dfree(l.e); dfree(l.f); dfree(l.wf); dfree(l.we);
+        l.u0 = l.u1 = l.e = l.f = l.wf = l.we = nullptr;
     }
     dfree(c->V); dfree(c->Z); dfree(c->W); dfree(c->W2); dfree(c->Bint); dfree(c->X);
     dfree(c->R); dfree(c->abi_in); dfree(c->abi_out); dfree(c->partial); dfree(c->small);
@@ -349,11 +360,17 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
         if (l > 0) {
             CUDA_TRY(c, dalloc(&c->lv[l].e, b));
             CUDA_TRY(c, dalloc(&c->lv[l].f, b));
+            if (c->p.cycle_gamma == 2) {
+                CUDA_TRY(c, dalloc(&c->lv[l].wf, b));
+                CUDA_TRY(c, dalloc(&c->lv[l].we, b));
+            }
         }
     }
     const size_t zel = c->p.prec == HELM_PLAIN_C128 ? sizeof(c128) : sizeof(c64);
-    CUDA_TRY(c, dalloc(&c->V, vec * (m + 1)));
-    CUDA_TRY(c, dalloc(&c->Z, zel * (size_t)N * s * m));
+    // block BiCGSTAB keeps six FP64 blocks (R, P, V, S, T, shadow) in V and
+    // two preconditioned blocks in Z
+    CUDA_TRY(c, dalloc(&c->V, vec * std::max(m + 1, 6)));
+    CUDA_TRY(c, dalloc(&c->Z, zel * (size_t)N * s * std::max(m, 2)));
     CUDA_TRY(c, dalloc(&c->W, vec));
     CUDA_TRY(c, dalloc(&c->W2, vec));
     CUDA_TRY(c, dalloc(&c->Bint, vec));
@@ -368,7 +385,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     CUDA_TRY(c, dalloc(&c->partial, sizeof(c128) * pe));
     // small: 2 H passes + G + T + Y + norms
     long long blk = (long long)G * sb * sb;
-    c->small_elems = 2 * (m + 1) * blk + 2 * blk + (long long)m * blk + 4LL * s + 64;
+    c->small_elems = std::max(2 * (m + 1) * blk + 2 * blk + (long long)m * blk, 10 * blk) + 4LL * s + 64;
     CUDA_TRY(c, dalloc(&c->small, sizeof(c128) * c->small_elems));
     CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->hsmall), sizeof(c128) * c->small_elems));
     CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
@@ -865,6 +882,192 @@ finish:
     return result;
 }
 
+// ---------------------------------------------------------------------------
+// block BiCGSTAB (Sec. 5.3 "W-BiCG": El Guennouni, Jbilou and Sadok's block
+// BiCGSTAB preconditioned by W-cycles), per group of `block` columns
+// ---------------------------------------------------------------------------
+
+// G Y = Rhs for one group (n x n, row-major): Gaussian elimination with
+// partial pivoting; a pivot below 1e-14 max|G| zeroes its row of Y.
+std::vector<cd> small_solve(const std::vector<cd>& G, const std::vector<cd>& Rhs, int n) {
+    std::vector<cd> A = G, Y = Rhs;
+    double scale = 0;
+    for (auto& v : A) scale = std::max(scale, std::abs(v));
+    std::vector<char> dead(n, 0);
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::abs(A[i * n + k]) > std::abs(A[p * n + k])) p = i;
+        if (p != k)
+            for (int j = 0; j < n; ++j) { std::swap(A[k * n + j], A[p * n + j]); std::swap(Y[k * n + j], Y[p * n + j]); }
+        if (!(std::abs(A[k * n + k]) > 1e-14 * scale)) { dead[k] = 1; continue; }
+        for (int i = k + 1; i < n; ++i) {
+            cd f = A[i * n + k] / A[k * n + k];
+            for (int j = k; j < n; ++j) A[i * n + j] -= f * A[k * n + j];
+            for (int j = 0; j < n; ++j) Y[i * n + j] -= f * Y[k * n + j];
+        }
+    }
+    for (int k = n - 1; k >= 0; --k)
+        for (int j = 0; j < n; ++j) {
+            if (dead[k]) { Y[k * n + j] = 0.0; continue; }
+            cd v = Y[k * n + j];
+            for (int t = k + 1; t < n; ++t) v -= A[k * n + t] * Y[t * n + j];
+            Y[k * n + j] = v / A[k * n + k];
+        }
+    return Y;
+}
+
+template <typename ZT>
+helm_status bicgstab(helm_ctx* c, int s, double tol, helm_info* info) {
+    const long long N = c->N();
+    const long long vs = N * s;
+    const int sb = std::min(c->p.block, s);
+    const int G = (s + sb - 1) / sb;
+    const long long blk = (long long)G * sb * sb;
+    const size_t vbytes = sizeof(c128) * (size_t)vs;
+    c128 *R = c->V, *P = c->V + vs, *Vv = c->V + 2 * vs, *S = c->V + 3 * vs, *T = c->V + 4 * vs,
+         *Rt = c->V + 5 * vs;
+    cplx<ZT>* Ph = reinterpret_cast<cplx<ZT>*>(c->Z);
+    cplx<ZT>* Sh = Ph + vs;
+    helm::FineOp<double> opA = fine_op<double>(c, false);
+    // device small-matrix slots (each blk complex): 0..5 Grams, 6..7 [alpha; omega I], 8 beta-ish
+    c128* d = c->small;
+    cd* h = reinterpret_cast<cd*>(c->hsmall);
+    const bool emu = emulated(c);
+    const int maxit = std::max(1, c->p.restart * std::max(1, c->p.max_restarts));
+
+    std::vector<double> bn2;
+    helm_status st = colnorms(c, c->Bint, s, bn2);
+    if (st != HELM_OK) return st;
+    std::vector<double> bn(s), rel(s, 0.0);
+    for (int j = 0; j < s; ++j) {
+        if (!std::isfinite(bn2[j])) return fail(c, HELM_ERR_NONFINITE, "non-finite right-hand side");
+        bn[j] = std::sqrt(bn2[j]);
+    }
+    helm::launch_zero(c->L(), c->X, vbytes);
+    std::vector<int> iters(G, 0);
+    helm_status result = HELM_NOT_CONVERGED;
+    auto gram = [&](const c128* X, const c128* Y, int slot) {
+        helm::launch_gram(c->L(), X, 1, 0, Y, N, s, sb, c->partial, d + slot * blk, emu);
+    };
+    auto group_cols = [&](int g) { return std::min(sb, s - g * sb); };
+    auto get = [&](int slot, int g, int a, int b) { return h[slot * blk + (long long)g * sb * sb + a * sb + b]; };
+
+    for (int run = 0; run <= c->p.max_restarts; ++run) {
+        helm::launch_residual<double, helm::FineOp<double>>(c->L(), opA, c->X, c->Bint, R, s);
+        std::vector<double> rn2;
+        st = colnorms(c, R, s, rn2);
+        if (st != HELM_OK) return st;
+        bool all = true;
+        for (int j = 0; j < s; ++j) {
+            if (!std::isfinite(rn2[j])) { result = fail(c, HELM_ERR_NONFINITE, "non-finite residual"); goto done; }
+            rel[j] = bn[j] > 0 ? std::sqrt(rn2[j]) / bn[j] : 0.0;
+            all = all && rel[j] <= tol;
+        }
+        if (all) { result = HELM_OK; break; }
+        if (run == c->p.max_restarts) break;
+        CUDA_TRY(c, cudaMemcpyAsync(Rt, R, vbytes, cudaMemcpyDeviceToDevice, c->st));
+        CUDA_TRY(c, cudaMemcpyAsync(P, R, vbytes, cudaMemcpyDeviceToDevice, c->st));
+        std::vector<char> gdone(G, 0);
+        for (int g = 0; g < G; ++g) {
+            bool ok = true;
+            for (int j = g * sb; j < g * sb + group_cols(g); ++j) ok = ok && rel[j] <= tol;
+            gdone[g] = ok;
+        }
+        for (int k = 0; k < maxit; ++k) {
+            // Ph = M P, V = A Ph ; alpha = (Rt^H V)^{-1} Rt^H R
+            cycle<ZT, double>(c, 0, P, Ph, s);
+            helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), opA, Ph, Vv, s);
+            gram(Rt, Vv, 0);
+            gram(Rt, R, 1);
+            CUDA_TRY(c, cudaMemcpyAsync(h, d, sizeof(c128) * 2 * blk, cudaMemcpyDeviceToHost, c->st));
+            st = sync(c);
+            if (st != HELM_OK) return st;
+            std::vector<std::vector<cd>> Gv(G), alpha(G);
+            cd* ha = h + 6 * blk;          // [alpha; omega I] for the X update (two blocks)
+            std::memset(ha, 0, sizeof(c128) * 2 * blk);
+            for (int g = 0; g < G; ++g) {
+                int n = group_cols(g);
+                std::vector<cd> Gm(n * n), rhs(n * n);
+                for (int a = 0; a < n; ++a)
+                    for (int b = 0; b < n; ++b) { Gm[a * n + b] = get(0, g, a, b); rhs[a * n + b] = get(1, g, a, b); }
+                Gv[g] = Gm;
+                alpha[g] = gdone[g] ? std::vector<cd>(n * n, 0.0) : small_solve(Gm, rhs, n);
+                for (int a = 0; a < n; ++a)
+                    for (int b = 0; b < n; ++b) ha[(long long)g * sb * sb + a * sb + b] = alpha[g][a * n + b];
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(d + 6 * blk, ha, sizeof(c128) * blk, cudaMemcpyHostToDevice, c->st));
+            // S = R - V alpha ; Sh = M S ; T = A Sh
+            CUDA_TRY(c, cudaMemcpyAsync(S, R, vbytes, cudaMemcpyDeviceToDevice, c->st));
+            helm::launch_combine<double>(c->L(), S, 1.0, -1.0, Vv, 1, 0, d + 6 * blk, N, s, sb, emu, c->csplit);
+            cycle<ZT, double>(c, 0, S, Sh, s);
+            helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), opA, Sh, T, s);
+            gram(Rt, T, 2);
+            gram(T, S, 3);
+            gram(T, T, 4);
+            gram(S, S, 5);
+            CUDA_TRY(c, cudaMemcpyAsync(h + 2 * blk, d + 2 * blk, sizeof(c128) * 4 * blk, cudaMemcpyDeviceToHost, c->st));
+            st = sync(c);
+            if (st != HELM_OK) return st;
+            // omega per group, residual estimates, beta
+            cd* hw = h + 7 * blk;          // omega I
+            cd* hb = h + 8 * blk;          // [beta; -omega beta] for the P update (two blocks)
+            std::memset(hw, 0, sizeof(c128) * blk);
+            std::memset(hb, 0, sizeof(c128) * 2 * blk);
+            bool all_done = true;
+            for (int g = 0; g < G; ++g) {
+                int n = group_cols(g);
+                if (gdone[g]) continue;
+                cd ts = 0.0, tt = 0.0;
+                for (int a = 0; a < n; ++a) { ts += get(3, g, a, a); tt += get(4, g, a, a); }
+                cd om = std::abs(tt) > 0 ? ts / tt : cd(0.0);
+                bool ok = true;
+                for (int a = 0; a < n; ++a) {
+                    double r2 = get(5, g, a, a).real() - 2.0 * (std::conj(om) * get(3, g, a, a)).real() +
+                                std::norm(om) * get(4, g, a, a).real();
+                    int j = g * sb + a;
+                    double e = bn[j] > 0 ? std::sqrt(std::max(r2, 0.0)) / bn[j] : 0.0;
+                    ok = ok && e <= tol;
+                }
+                iters[g] += 2;
+                std::vector<cd> rhs(n * n);
+                for (int a = 0; a < n; ++a)
+                    for (int b = 0; b < n; ++b) rhs[a * n + b] = -get(2, g, a, b);
+                std::vector<cd> beta = ok ? std::vector<cd>(n * n, 0.0) : small_solve(Gv[g], rhs, n);
+                for (int a = 0; a < n; ++a) {
+                    hw[(long long)g * sb * sb + a * sb + a] = om;
+                    for (int b = 0; b < n; ++b) {
+                        hb[(long long)g * sb * sb + a * sb + b] = beta[a * n + b];
+                        hb[blk + (long long)g * sb * sb + a * sb + b] = -om * beta[a * n + b];
+                    }
+                }
+                if (ok) gdone[g] = 1;
+                else all_done = false;
+            }
+            CUDA_TRY(c, cudaMemcpyAsync(d + 7 * blk, hw, sizeof(c128) * 3 * blk, cudaMemcpyHostToDevice, c->st));
+            // X += Ph alpha + Sh omega ; R = S - omega T ; P = R + P beta - V omega beta
+            helm::launch_combine<ZT>(c->L(), c->X, 1.0, 1.0, Ph, 2, vs, d + 6 * blk, N, s, sb, emu, c->csplit);
+            CUDA_TRY(c, cudaMemcpyAsync(R, S, vbytes, cudaMemcpyDeviceToDevice, c->st));
+            helm::launch_combine<double>(c->L(), R, 1.0, -1.0, T, 1, 0, d + 7 * blk, N, s, sb, emu, c->csplit);
+            if (all_done) break;
+            CUDA_TRY(c, cudaMemcpyAsync(c->W, R, vbytes, cudaMemcpyDeviceToDevice, c->st));
+            helm::launch_combine<double>(c->L(), c->W, 1.0, 1.0, P, 2, vs, d + 8 * blk, N, s, sb, emu, c->csplit);
+            CUDA_TRY(c, cudaMemcpyAsync(P, c->W, vbytes, cudaMemcpyDeviceToDevice, c->st));
+        }
+    }
+done:
+    if (info) {
+        for (int j = 0; j < s; ++j) {
+            if (info->iters) info->iters[j] = iters[j / sb];
+            if (info->relres) info->relres[j] = rel[j];
+            if (info->status)
+                info->status[j] = (result == HELM_ERR_NONFINITE) ? HELM_ERR_NONFINITE
+                                  : (rel[j] <= tol ? HELM_OK : HELM_NOT_CONVERGED);
+        }
+    }
+    return result;
+}
+
 helm_status solve_internal(helm_ctx* c, const c128* Qd, int s, double tol, c128* Ud,
                            helm_info* info, bool conjugate) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
@@ -875,7 +1078,10 @@ helm_status solve_internal(helm_ctx* c, const c128* Qd, int s, double tol, c128*
     if (st != HELM_OK) return st;
     const long long N = c->N();
     helm::launch_to_internal(c->L(), Qd, c->Bint, N, s, conjugate);
-    if (c->p.prec == HELM_PLAIN_C128)
+    if (c->p.krylov == 1)
+        st = c->p.prec == HELM_PLAIN_C128 ? bicgstab<double>(c, s, tol, info)
+                                          : bicgstab<float>(c, s, tol, info);
+    else if (c->p.prec == HELM_PLAIN_C128)
         st = fgmres<double>(c, s, tol, info);
     else
         st = fgmres<float>(c, s, tol, info);
@@ -930,6 +1136,8 @@ void helm_default_params(helm_params* p) {
     p->prec = HELM_PLAIN_C128;
     p->learned_weights = nullptr;
     p->coarse_tf32x3 = 0;
+    p->cycle_gamma = 1;
+    p->krylov = 0;
 }
 
 helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_params* p,
@@ -945,6 +1153,14 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         return fail(nullptr, HELM_ERR_ARG, "bad precision policy");
     if (p->prec == HELM_MIXED_C64_LEARNED && (p->dim != 2 || !p->learned_weights))
         return fail(nullptr, HELM_ERR_ARG, "the learned stage needs a 2D grid and learned_weights");
+    if ((p->cycle_gamma != 1 && p->cycle_gamma != 2) || (p->krylov != 0 && p->krylov != 1))
+        return fail(nullptr, HELM_ERR_ARG, "cycle_gamma must be 1 or 2, krylov 0 or 1");
+    if (p->krylov == 1 && p->prec == HELM_MIXED_C64_LEARNED)
+        return fail(nullptr, HELM_ERR_ARG, "block BiCGSTAB needs a fixed preconditioner (no learned stage)");
+    if (p->krylov == 1 && p->prec == HELM_MIXED_C64 && p->block > 2)
+        return fail(nullptr, HELM_ERR_ARG,
+                    "block BiCGSTAB with the complex64 cycle needs block <= 2 (larger blocks diverge: "
+                    "the cycle's FP32 rounding makes the preconditioner slightly non-stationary)");
     int nodes[3] = {1, 1, 1};
     for (int k = 0; k < p->dim; ++k) {
         if (p->n[k] < 1) return fail(nullptr, HELM_ERR_ARG, "cells per axis must be >= 1");
@@ -1294,6 +1510,8 @@ extern "C" {
 helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, int s) {
     if (!c || prec < 0 || prec > 1 || !f || !z || s < 1)
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_vcycle_noalloc");
+    if (c->p.cycle_gamma != 1)
+        return fail(c, HELM_ERR_ARG, "helm_vcycle_noalloc runs V-cycles only (cycle_gamma 1)");
     const size_t esz = prec == 0 ? sizeof(c128) : sizeof(c64);
     // level 0 needs two buffers (u0, u1); every coarser level four (u0, u1, e, f)
     size_t need = 0;

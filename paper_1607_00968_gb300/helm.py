@@ -40,7 +40,8 @@ class HelmParams(ctypes.Structure):
                 ("jacobi_w", ctypes.c_double), ("restart", ctypes.c_int),
                 ("block", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("prec", ctypes.c_int), ("learned_weights", ctypes.c_void_p),
-                ("coarse_tf32x3", ctypes.c_int)]
+                ("coarse_tf32x3", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
+                ("krylov", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -165,7 +166,7 @@ class Solver:
                  levels: int = 3, pre: int = 2, post: int = 2, jacobi_w: float = 0.8,
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
                  prec: str = "c128", stream=None, coarse_tf32x3: bool = False,
-                 learned_weights=None):
+                 learned_weights=None, cycle: str = "V", krylov: str = "fgmres"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libhelm needs a CUDA device")
@@ -191,6 +192,8 @@ class Solver:
         p.restart, p.block, p.max_restarts = int(restart), int(block), int(max_restarts)
         p.prec = PREC[prec]
         p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
+        p.cycle_gamma = {"V": 1, "W": 2}[cycle]
+        p.krylov = {"fgmres": 0, "bicgstab": 1}[krylov]
         self.learned_weights = learned_weights        # keeps the blob alive
         p.learned_weights = _ptr(learned_weights) if learned_weights is not None else None
         self.params = p

@@ -280,6 +280,8 @@ def test_bad_arguments_raise(H):
     m, g, h, om = layered((32, 16))
     with pytest.raises(H.HelmError):
         H.Solver(m, g, h, om, levels=6)       # 16 cells not divisible by 2^5
+    with pytest.raises(H.HelmError):
+        H.Solver(m, g, h, om, levels=2, prec="c64", krylov="bicgstab", block=4)
     S = H.Solver(m, g, h, om, levels=2)
     with pytest.raises(H.HelmError):
         S.solve(dev(np.ones((1, S.N), dtype=complex)), tol=-1.0)
@@ -317,3 +319,44 @@ def test_solve_batch_matches_single_solves(H):
         A = O.helmholtz_matrix(P.m, P.gamma, P.omega, P.h)
         assert np.all(O.relres(A, U.cpu().numpy().T, Q.cpu().numpy().T) <= 1e-8)
         np.testing.assert_array_equal(inf.iters, i1.iters)
+
+
+# --------------------------------------------------------------------------
+# W-cycle and block BiCGSTAB (Sec. 5.3 "W-BiCG")
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cells,levels", [((40, 24), 3), ((16, 12, 8), 3)])
+def test_wcycle_matches_oracle(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels, cycle="W")
+    Hh = O.Hierarchy(O.helmholtz_matrix(m, g, om, h, 0.5), m.shape, levels)
+    rng = np.random.default_rng(40)
+    f = crand(rng, S.N, 6)
+    z = S.vcycle(dev(f), "c128").cpu().numpy()
+    assert rel(z, O.vcycle(Hh, f, gamma=2)) < 1e-11
+    z32 = S.vcycle(dev(f), "c64").cpu().numpy()
+    assert rel(z32, O.vcycle(Hh, f, gamma=2)) < 5e-3
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("cells,levels,s,block", [((64, 32), 3, 6, 3), ((16, 16, 8), 3, 4, 4)])
+def test_bicgstab_matches_oracle(H, prec, cells, levels, s, block):
+    if prec == "c64":
+        block = 1          # the complex64 cycle supports block BiCGSTAB with blocks <= 2
+    m, g, h, om = layered(cells, width=6)
+    S = H.Solver(m, g, h, om, levels=levels, block=block, prec=prec, cycle="W", krylov="bicgstab",
+                 restart=50, max_restarts=5)
+    So = O.Solver(m, g, om, h, levels=levels)
+    shape = m.shape
+    pos = I.line_positions(shape, s, 2, 6) if len(cells) == 2 else \
+        [(0, shape[1] // 2, 2 + 2 * k) for k in range(s)]
+    Q = I.point_sources(shape, pos, h)
+    U, info, st = S.solve(dev(Q), tol=1e-10)
+    U = U.cpu().numpy()
+    assert np.all(O.relres(So.A, U.T, Q.T) <= 1e-10)
+    Uo, infos = So.solve_bicgstab(Q.T.copy(), tol=1e-10, block=block, gamma=2)
+    for k in range(s):
+        assert rel(U[k], Uo[:, k]) <= 1e-5
+    if prec == "c128":
+        for gi, inf in enumerate(infos):
+            assert abs(int(info.iters[gi * block]) - inf.iters) <= 4, (info.iters, inf.iters)

@@ -420,3 +420,76 @@ def test_zero_and_duplicate_columns():
     np.testing.assert_allclose(U[:, 2], U[:, 0], rtol=1e-8)
     np.testing.assert_allclose(U[:, 3], 2 * U[:, 0], rtol=1e-8)
     assert np.all(O.relres(S.A, U, Q) <= 1e-10)
+
+
+# --------------------------------------------------------------------------
+# block BiCGSTAB with W-cycles (Sec. 5.3 "W-BiCG")
+# --------------------------------------------------------------------------
+
+def test_wcycle_is_linear_and_better_than_vcycle_on_poisson():
+    shape = I.node_shape((32, 32))
+    M = O.helmholtz_matrix(np.ones(shape), np.zeros(shape), 0.0, 1.0)
+    H = O.Hierarchy(M, shape, 4)
+    rng = np.random.default_rng(30)
+    f1, f2 = crand(rng, M.shape[0], 1), crand(rng, M.shape[0], 1)
+    np.testing.assert_allclose(O.vcycle(H, 2 * f1 - 1j * f2, gamma=2),
+                               2 * O.vcycle(H, f1, gamma=2) - 1j * O.vcycle(H, f2, gamma=2),
+                               rtol=1e-11)
+    e_v = np.linalg.norm(f1 - M @ O.vcycle(H, f1, gamma=1))
+    e_w = np.linalg.norm(f1 - M @ O.vcycle(H, f1, gamma=2))
+    assert e_w < e_v
+
+
+def scalar_bicgstab(A, Mp, b, iters):
+    """van der Vorst's BiCGSTAB for one right-hand side (complex, r_hat^H
+    products), right-preconditioned: the s = 1 case of the block method."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rh = r.copy()
+    rho = alpha = omega = 1.0
+    v = p = np.zeros_like(b)
+    hist = []
+    for _ in range(iters):
+        rho_new = np.vdot(rh, r)
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = Mp(p)
+        v = A @ ph
+        alpha = rho_new / np.vdot(rh, v)
+        s = r - alpha * v
+        sh = Mp(s)
+        t = A @ sh
+        omega = np.vdot(t, s) / np.vdot(t, t)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho = rho_new
+        hist.append(np.linalg.norm(r))
+    return x, hist
+
+
+def test_block_bicgstab_single_column_is_scalar_bicgstab():
+    p = small_problem((16, 16), seed=5)
+    S = O.Solver(p["m"], p["gamma"], p["omega"], p["h"], levels=2)
+    rng = np.random.default_rng(31)
+    b = crand(rng, S.A.shape[0])
+    Mp = lambda v: S.precond(v[:, None], 2)[:, 0]
+    xs, hist = scalar_bicgstab(S.A, Mp, b, 4)
+    X, info = O.block_bicgstab(S.A, lambda V: S.precond(V, 2), b[:, None], tol=1e-300, maxit=4,
+                               max_restarts=1)
+    np.testing.assert_allclose(np.array(info.history)[:, 0] * np.linalg.norm(b), hist, rtol=1e-8)
+    np.testing.assert_allclose(X[:, 0], xs, rtol=1e-8, atol=1e-12 * np.abs(xs).max())
+
+
+def test_block_bicgstab_converges_and_keeps_biorthogonality():
+    for cells, lv in (((16, 8), 2), ((32, 16), 3), ((8, 8, 4), 2)):
+        shape = I.node_shape(cells)
+        g = I.absorbing_gamma(shape, 2)
+        rng = np.random.default_rng(32)
+        S = O.Solver(rng.uniform(0.5, 1.5, shape), g, 1.2, 1.0, levels=lv)
+        Q = crand(rng, S.A.shape[0], 3)
+        U, infos = S.solve_bicgstab(Q, tol=1e-11, block=3, gamma=2)
+        assert infos[0].converged
+        Ud = O.dense_solve(S.A, Q)
+        assert np.linalg.norm(U - Ud) <= 1e-8 * np.linalg.norm(Ud)
+        # alpha makes S orthogonal to the shadow block (while S is above rounding)
+        assert max(infos[0].biortho[:3]) < 1e-10
