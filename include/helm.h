@@ -305,6 +305,36 @@ helm_status helm_learned_loss(const float* pred, const float* t, int batch, long
                               void* grad, float* loss_out, void* stream);
 
 /* ---------------------------------------------------------------------
+ * FWI sensitivities (Sec. 2.4 Eq. fwisens; data Eq. data; misfit Eq. minp
+ * without regularisation).  In this library's sign convention
+ *     J = du/dm = w^2 A^{-1} diag((1 - i g) u),
+ * data are the fields sampled at receiver nodes recv (device int array of
+ * nrec node indices), and for real m
+ *     J^T w = sum over sources Re(conj(w^2 (1 - i g) u_j) lambda_j),
+ *     lambda_j = A^{-H} P w_j  (one adjoint solve per source).
+ * Fields U: device, ABI layout (s x N), complex128, or 16-bit pairs
+ * (half re, half im; fields_half = 1), the storage Sec. 2.4 uses for the
+ * forward fields.  Data blocks (W, d_obs, jv output): device complex128,
+ * s x nrec (column j = source j).  Solves use the context's solver and tol;
+ * each call allocates its temporaries.
+ * ------------------------------------------------------------------- */
+/* U16[e] = (half) U[e] for N*s complex values. */
+helm_status helm_fields_to_half(const void* U, long long N, int s, void* U16, void* stream);
+/* out = P^T J v per source (v: device double[N]). */
+helm_status helm_fwi_jv(helm_ctx* ctx, const void* fields, int fields_half, int s, const double* v,
+                        const int* recv, int nrec, double tol, void* out);
+/* out[k] = (J^T w)_k summed over the s sources (device double[N]). */
+helm_status helm_fwi_jtw(helm_ctx* ctx, const void* fields, int fields_half, int s, const void* W,
+                         const int* recv, int nrec, double tol, double* out);
+/* Forward solve of Q, data residual U[recv] - d_obs, misfit (host, may be
+   NULL) = 1/2 sum |residual|^2, gradient grad = J^T residual (device
+   double[N]); store_half keeps the forward fields in 16 bits for the
+   gradient product; U_out (device, may be NULL) receives the fields. */
+helm_status helm_fwi_gradient(helm_ctx* ctx, const void* Q, int s, const void* d_obs, const int* recv,
+                              int nrec, double tol, int store_half, double* grad, double* misfit,
+                              void* U_out);
+
+/* ---------------------------------------------------------------------
  * Per-kernel profiler (the per-RHS timing of Sec. 5.3's table, broken down
  * by kernel).  When enabled, every launch on the context is bracketed by a
  * CUDA event pair on the context's stream and tagged with its algorithmic

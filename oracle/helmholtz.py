@@ -523,6 +523,51 @@ class Solver:
         return np.conj(U), infos
 
 
+# --------------------------------------------------------------------------
+# FWI sensitivities (Sec. 2.4 Eq. fwisens; data Eq. data; misfit Eq. minp)
+# --------------------------------------------------------------------------
+#
+# In this sign convention A(m) = -Lap_h - w^2 diag(m (1 - i g)), so
+# dA/dm_k = -w^2 (1 - i g_k) e_k e_k^T and differentiating A u = q gives
+#     J = du/dm = w^2 A^{-1} diag((1 - i g) u)
+# (the paper's J up to the sign of u).  With receivers R (node indices) the
+# data are P^T u = u[R]; for real m, J^T w = Re(J^H P w) =
+#     w^2 Re(conj((1 - i g) u) lambda),  lambda = A^{-H} P w,
+# and the gradient of Phi = 1/2 sum_s ||u_s[R] - d_s||^2 is J^T (P^T u - d),
+# summed over the sources.
+
+
+def dA_dm(gamma, omega: float) -> np.ndarray:
+    """w^2 (1 - i g): minus the derivative of A's diagonal w.r.t. m."""
+    return omega * omega * (1.0 - 1j * np.asarray(gamma, dtype=np.float64).ravel())
+
+
+def fwi_jv(solve, gamma, omega, U, v, recv):
+    """P^T J v for every source: w^2 A^{-1} (dA_dm * U * v) sampled at recv.
+    solve(B) returns A^{-1} B for B of shape (N, s)."""
+    rhs = dA_dm(gamma, omega)[:, None] * U * np.asarray(v, dtype=np.float64).ravel()[:, None]
+    return solve(rhs)[recv, :]
+
+
+def fwi_jtw(adjoint, gamma, omega, U, W, recv):
+    """J^T w summed over sources (real, length N): lambda = A^{-H} P w,
+    sum_s Re(conj(dA_dm * u_s) lambda_s).  adjoint(B) returns A^{-H} B."""
+    N = U.shape[0]
+    PW = np.zeros((N, W.shape[1]), dtype=np.complex128)
+    PW[recv, :] = W
+    Lam = adjoint(PW)
+    return np.sum(np.real(np.conj(dA_dm(gamma, omega)[:, None] * U) * Lam), axis=1)
+
+
+def fwi_misfit_gradient(solve, adjoint, gamma, omega, Q, recv, d_obs):
+    """(Phi, grad, U): Phi = 1/2 sum_s ||u_s[recv] - d_s||^2 and its gradient
+    with respect to m (Eq. minp without regularisation, unit covariance)."""
+    U = solve(Q)
+    D = U[recv, :] - d_obs
+    phi = 0.5 * float(np.sum(np.abs(D) ** 2))
+    return phi, fwi_jtw(adjoint, gamma, omega, U, D, recv), U
+
+
 def relres(Amat, U, Q) -> np.ndarray:
     """Per-column true relative residual ||q_i - A u_i|| / ||q_i|| in FP64."""
     R = Q - apply(Amat, U)

@@ -89,6 +89,25 @@ void launch_select_better(const Launch& L, const c64* z2, c64* z1, long long N, 
 void launch_learned_residual(const Launch& L, const FineOp<float>& op, const c128* f, const c64* z,
                              c64* r, int s, float* rho2, float* rho);
 
+// ---------------- FWI sensitivity products (fwi.cu) ----------------
+
+// dadm[k] = w^2 (1 - i g_k) (minus the derivative of A's diagonal w.r.t. m)
+void launch_dadm(const Launch& L, const double* gamma, double omega, long long N, c128* dadm);
+// complex128 -> 16-bit pairs (half re, half im)
+void launch_to_half(const Launch& L, const c128* u, long long n, void* u16);
+// rhs = dadm * u * v (ABI layout, s columns)
+void launch_jv_rhs(const Launch& L, const void* fields, int half, long long N, int s, const c128* dadm,
+                   const double* v, c128* rhs);
+// out[j][r] = X[j][recv[r]] - d[j][r] (d may be null)
+void launch_gather(const Launch& L, const c128* X, long long N, int s, const int* recv, int nrec,
+                   const c128* d, c128* out);
+// out = P W (zeroed first; repeated receivers add)
+void launch_scatter(const Launch& L, const c128* W, long long N, int s, const int* recv, int nrec,
+                    c128* out);
+// g[k] = sum_j Re(conj(dadm_k u_jk) lam_jk)
+void launch_grad(const Launch& L, const void* fields, int half, const c128* lam, long long N, int s,
+                 const c128* dadm, double* g);
+
 // ---------------- set-up (mg.cu) ----------------
 
 // c_A = omega^2 m (1 - i gamma), c_M = omega^2 m (1 - i (gamma + shift)),

@@ -138,6 +138,7 @@ struct helm_ctx {
     c64* Minv32 = nullptr;
     float* Ap = nullptr;      // tf32-rounded interleaved inverse for the tensor-core solve
     float* dense_scratch = nullptr;
+    c128* dadm = nullptr;     // omega^2 (1 - i gamma) per node (FWI sensitivities)
     // learned stage
     float* kappa = nullptr;   // omega^2 m h^2 per node
     c64* lr_r = nullptr;      // residual of the cycle's result
@@ -1218,6 +1219,8 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         helm::launch_galerkin(L, c->lv[l - 1].g, c->lv[l].g, c->lv[l - 1].coef, c->lv[l].coef);
         helm::launch_diag_inv(L, c->lv[l].g, c->lv[l].coef, c->lv[l].dinv);
     }
+    SETUP_TRY(dalloc(&c->dadm, sizeof(c128) * N0));
+    helm::launch_dadm(L, dg, p->omega, N0, c->dadm);
     SETUP_TRY(dalloc(&c->kappa, sizeof(float) * N0));
     helm::launch_kappa(L, c->cA, N0, p->h * p->h, c->kappa);
     helm::launch_round_c64(L, c->cA, c->cA32, N0);
@@ -1357,6 +1360,7 @@ void helm_destroy(helm_ctx* c) {
     dfree(c->cA); dfree(c->cM); dfree(c->cA32); dfree(c->cM32); dfree(c->Minv); dfree(c->Minv32);
     dfree(c->Ap);
     dfree(c->kappa);
+    dfree(c->dadm);
     delete c;
 }
 
@@ -1676,6 +1680,92 @@ helm_status helm_learned_loss(const float* pred, const float* t, int batch, long
         return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_learned_loss");
     helm::launch_loss(bare_launch(stream), pred, t, batch, (int)P, sums, grad, loss_out);
     return check_launch(stream);
+}
+
+helm_status helm_fields_to_half(const void* U, long long N, int s, void* U16, void* stream) {
+    if (!U || !U16 || N < 1 || s < 1) return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_fields_to_half");
+    helm::launch_to_half(bare_launch(stream), static_cast<const c128*>(U), N * s, U16);
+    return check_launch(stream);
+}
+
+helm_status helm_fwi_jv(helm_ctx* c, const void* fields, int fields_half, int s, const double* v,
+                        const int* recv, int nrec, double tol, void* out) {
+    if (!c || !fields || !v || !recv || !out || s < 1 || nrec < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_jv");
+    const long long N = c->N();
+    c128 *rhs = nullptr, *w = nullptr;
+    CUDA_TRY(c, dalloc(&rhs, sizeof(c128) * (size_t)N * s));
+    CUDA_TRY(c, dalloc(&w, sizeof(c128) * (size_t)N * s));
+    helm::launch_jv_rhs(c->L(), fields, fields_half, N, s, c->dadm, v, rhs);
+    helm_status st = helm_solve(c, rhs, s, tol, w, nullptr);
+    if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
+        helm::launch_gather(c->L(), w, N, s, recv, nrec, nullptr, static_cast<c128*>(out));
+        helm_status st2 = sync(c);
+        if (st2 != HELM_OK) st = st2;
+    }
+    dfree(rhs);
+    dfree(w);
+    return st;
+}
+
+helm_status helm_fwi_jtw(helm_ctx* c, const void* fields, int fields_half, int s, const void* W,
+                         const int* recv, int nrec, double tol, double* out) {
+    if (!c || !fields || !W || !recv || !out || s < 1 || nrec < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_jtw");
+    const long long N = c->N();
+    c128 *pw = nullptr, *lam = nullptr;
+    CUDA_TRY(c, dalloc(&pw, sizeof(c128) * (size_t)N * s));
+    CUDA_TRY(c, dalloc(&lam, sizeof(c128) * (size_t)N * s));
+    helm::launch_scatter(c->L(), static_cast<const c128*>(W), N, s, recv, nrec, pw);
+    helm_status st = helm_adjoint(c, pw, s, tol, lam, nullptr);
+    if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
+        helm::launch_grad(c->L(), fields, fields_half, lam, N, s, c->dadm, out);
+        helm_status st2 = sync(c);
+        if (st2 != HELM_OK) st = st2;
+    }
+    dfree(pw);
+    dfree(lam);
+    return st;
+}
+
+helm_status helm_fwi_gradient(helm_ctx* c, const void* Q, int s, const void* d_obs, const int* recv,
+                              int nrec, double tol, int store_half, double* grad, double* misfit,
+                              void* U_out) {
+    if (!c || !Q || !d_obs || !recv || !grad || s < 1 || nrec < 1)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_gradient");
+    const long long N = c->N();
+    c128 *U = nullptr, *D = nullptr;
+    void* U16 = nullptr;
+    CUDA_TRY(c, dalloc(&U, sizeof(c128) * (size_t)N * s));
+    CUDA_TRY(c, dalloc(&D, sizeof(c128) * (size_t)nrec * s));
+    helm_status st = helm_solve(c, Q, s, tol, U, nullptr);
+    if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
+        helm::launch_gather(c->L(), U, N, s, recv, nrec, static_cast<const c128*>(d_obs), D);
+        if (misfit) {
+            std::vector<c128> hD((size_t)nrec * s);
+            cudaMemcpyAsync(hD.data(), D, sizeof(c128) * hD.size(), cudaMemcpyDeviceToHost, c->st);
+            helm_status st2 = sync(c);
+            if (st2 != HELM_OK) st = st2;
+            double phi = 0.0;
+            for (auto& v : hD) phi += v.re * v.re + v.im * v.im;
+            *misfit = 0.5 * phi;
+        }
+        const void* fields = U;
+        if (store_half) {
+            // keep the forward fields in 16 bits (32 bits per complex unknown)
+            if (dalloc(&U16, sizeof(float) * (size_t)N * s) == cudaSuccess) {
+                helm::launch_to_half(c->L(), U, N * s, U16);
+                fields = U16;
+            }
+        }
+        if (U_out) cudaMemcpyAsync(U_out, U, sizeof(c128) * (size_t)N * s, cudaMemcpyDeviceToDevice, c->st);
+        helm_status st3 = helm_fwi_jtw(c, fields, U16 ? 1 : 0, s, D, recv, nrec, tol, grad);
+        if (st3 != HELM_OK && st == HELM_OK) st = st3;
+    }
+    dfree(U);
+    dfree(D);
+    dfree(U16);
+    return st;
 }
 
 int helm_profile_kernel_count(void) { return helm::KID_COUNT; }

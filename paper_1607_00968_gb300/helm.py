@@ -30,7 +30,8 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_profile_read", "helm_vcycle_noalloc", "helm_learned_layers",
            "helm_learned_blob_bytes", "helm_learned_layer", "helm_conv3x3", "helm_conv3x3_wgrad",
            "helm_conv3x3_flip", "helm_adam", "helm_learned_input", "helm_learned_target",
-           "helm_learned_loss"]
+           "helm_learned_loss", "helm_fields_to_half", "helm_fwi_jv", "helm_fwi_jtw",
+           "helm_fwi_gradient"]
 
 
 class HelmParams(ctypes.Structure):
@@ -104,6 +105,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_learned_input": (i, [vp, vp, vp, i, vp, vp]),
         "helm_learned_target": (i, [vp, ll, i, vp, ctypes.c_float, vp, vp]),
         "helm_learned_loss": (i, [vp, vp, i, ll, vp, vp, vp, vp]),
+        "helm_fields_to_half": (i, [vp, ll, i, vp, vp]),
+        "helm_fwi_jv": (i, [vp, vp, i, i, vp, vp, i, d, vp]),
+        "helm_fwi_jtw": (i, [vp, vp, i, i, vp, vp, i, d, vp]),
+        "helm_fwi_gradient": (i, [vp, vp, i, vp, vp, i, d, i, vp, P(d), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,6 +270,50 @@ class Solver:
         if check:
             self._check(st, (HELM_OK,))
         return info, st
+
+    # -- FWI sensitivities ----------------------------------------------------
+    def fwi_gradient(self, Q, d_obs, recv, tol=1e-8, store_half=False):
+        """(misfit, grad (N,) float64 device tensor, U (s, N)) for sources Q
+        (s, N), data d_obs (s, nrec) and receiver node indices recv."""
+        torch = self.torch
+        Q = self._block(Q)
+        s = Q.shape[0]
+        recv = torch.as_tensor(recv, dtype=torch.int32, device=Q.device)
+        d_obs = torch.as_tensor(d_obs).to(device=Q.device, dtype=torch.complex128).contiguous()
+        grad = torch.empty(self.N, dtype=torch.float64, device=Q.device)
+        U = torch.empty_like(Q)
+        phi = ctypes.c_double()
+        self._check(self.lib.helm_fwi_gradient(self.ctx, _ptr(Q), s, _ptr(d_obs), _ptr(recv),
+                                               recv.numel(), float(tol), 1 if store_half else 0,
+                                               _ptr(grad), ctypes.byref(phi), _ptr(U)))
+        return phi.value, grad, U
+
+    def fwi_jv(self, U, v, recv, tol=1e-8, half=False):
+        torch = self.torch
+        recv = torch.as_tensor(recv, dtype=torch.int32, device=U.device)
+        v = torch.as_tensor(v).to(device=U.device, dtype=torch.float64).contiguous()
+        s = U.shape[0]
+        out = torch.empty((s, recv.numel()), dtype=torch.complex128, device=U.device)
+        self._check(self.lib.helm_fwi_jv(self.ctx, _ptr(U), 1 if half else 0, s, _ptr(v), _ptr(recv),
+                                         recv.numel(), float(tol), _ptr(out)))
+        return out
+
+    def fwi_jtw(self, U, W, recv, tol=1e-8, half=False):
+        torch = self.torch
+        recv = torch.as_tensor(recv, dtype=torch.int32, device=U.device)
+        W = torch.as_tensor(W).to(device=U.device, dtype=torch.complex128).contiguous()
+        s = U.shape[0]
+        out = torch.empty(self.N, dtype=torch.float64, device=U.device)
+        self._check(self.lib.helm_fwi_jtw(self.ctx, _ptr(U), 1 if half else 0, s, _ptr(W), _ptr(recv),
+                                          recv.numel(), float(tol), _ptr(out)))
+        return out
+
+    def fields_to_half(self, U):
+        torch = self.torch
+        out = torch.empty(U.shape + (2,), dtype=torch.float16, device=U.device)
+        self._check(self.lib.helm_fields_to_half(_ptr(U), self.N, U.shape[0], _ptr(out),
+                                                 ctypes.c_void_p(self.stream.cuda_stream)))
+        return out
 
     # -- profiler ----------------------------------------------------------
     def profile(self, enable: bool = True):

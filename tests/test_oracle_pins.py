@@ -493,3 +493,65 @@ def test_block_bicgstab_converges_and_keeps_biorthogonality():
         assert np.linalg.norm(U - Ud) <= 1e-8 * np.linalg.norm(Ud)
         # alpha makes S orthogonal to the shadow block (while S is above rounding)
         assert max(infos[0].biortho[:3]) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# FWI sensitivities (Sec. 2.4 Eq. fwisens)
+# --------------------------------------------------------------------------
+
+def fwi_setup(seed=50):
+    cells = (8, 6)
+    shape = I.node_shape(cells)
+    rng = np.random.default_rng(seed)
+    m = rng.uniform(0.8, 1.2, shape)
+    g = I.absorbing_gamma(shape, 2) + 0.05
+    omega, h = 1.3, 1.0
+    N = int(np.prod(shape))
+    Q = np.zeros((N, 2), dtype=complex)
+    Q[3, 0] = Q[5, 1] = 1.0
+    recv = np.arange(0, shape[1])                 # top row
+    return m, g, omega, h, Q, recv, rng
+
+
+def test_fwi_gradient_finite_differences():
+    m, g, omega, h, Q, recv, rng = fwi_setup()
+
+    def solvers(mm):
+        A = O.helmholtz_matrix(mm, g, omega, h)
+        return (lambda B: O.dense_solve(A, B)), (lambda B: O.dense_solve(A.conj().T, B))
+
+    d_obs = crand(rng, recv.size, 2)
+    s, a = solvers(m)
+    phi, grad, _ = O.fwi_misfit_gradient(s, a, g, omega, Q, recv, d_obs)
+    eps = 1e-6
+    for k in rng.choice(m.size, 6, replace=False):
+        mp, mm_ = m.copy().ravel(), m.copy().ravel()
+        mp[k] += eps
+        mm_[k] -= eps
+        sp_, ap_ = solvers(mp.reshape(m.shape))
+        sm_, am_ = solvers(mm_.reshape(m.shape))
+        fp = O.fwi_misfit_gradient(sp_, ap_, g, omega, Q, recv, d_obs)[0]
+        fm = O.fwi_misfit_gradient(sm_, am_, g, omega, Q, recv, d_obs)[0]
+        num = (fp - fm) / (2 * eps)
+        assert abs(num - grad[k]) <= 1e-6 * max(1.0, abs(num)), (k, num, grad[k])
+
+
+def test_fwi_jv_jtw_dot_product():
+    """<J v, w>_R = v . J^T w for the real-to-complex linear map J."""
+    m, g, omega, h, Q, recv, rng = fwi_setup(51)
+    A = O.helmholtz_matrix(m, g, omega, h)
+    solve = lambda B: O.dense_solve(A, B)
+    adjoint = lambda B: O.dense_solve(A.conj().T, B)
+    U = solve(Q)
+    v = rng.standard_normal(m.size)
+    W = crand(rng, recv.size, 2)
+    Jv = O.fwi_jv(solve, g, omega, U, v, recv)
+    lhs = float(np.sum(np.real(np.conj(W) * Jv)))
+    rhs = float(v @ O.fwi_jtw(adjoint, g, omega, U, W, recv))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    # J v is the derivative of the sampled field along v
+    eps = 1e-6
+    Ap = O.helmholtz_matrix(m + eps * v.reshape(m.shape), g, omega, h)
+    Am = O.helmholtz_matrix(m - eps * v.reshape(m.shape), g, omega, h)
+    num = (O.dense_solve(Ap, Q) - O.dense_solve(Am, Q))[recv] / (2 * eps)
+    np.testing.assert_allclose(Jv, num, rtol=1e-6, atol=1e-9 * np.abs(num).max())
