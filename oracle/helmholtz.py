@@ -204,25 +204,56 @@ def jacobi(M: sp.csr_matrix, diag: np.ndarray, u, f, w: float, sweeps: int):
     return u
 
 
+def _kcycle_correction(H: Hierarchy, r: np.ndarray, level: int, pre, post, w):
+    """K-cycle coarse correction (Sec. 5.3 "K-cycles": the coarse system is
+    solved by two iterations of a flexible Krylov method preconditioned by the
+    cycle one level down), per column: two steps of flexible GMRES, written
+    as GCR(2):  z1 = C(r), w1 = M z1, a1 = w1^H r / w1^H w1, r2 = r - a1 w1;
+    z2 = C(r2), w2 = M z2, b = w1^H w2 / w1^H w1, w2 -= b w1, z2 -= b z1,
+    a2 = w2^H r2 / w2^H w2;  e = a1 z1 + a2 z2  (C = this level's K-cycle)."""
+    M = H.M[level]
+
+    def dots(a, b):
+        return np.sum(np.conj(a) * b, axis=0)
+
+    def ratio(num, den):
+        return np.where(den != 0, num / np.where(den != 0, den, 1), 0)
+
+    z1 = vcycle(H, r, level, pre, post, w, 3)
+    w1 = M @ z1
+    n1 = dots(w1, w1)
+    a1 = ratio(dots(w1, r), n1)
+    r2 = r - w1 * a1
+    z2 = vcycle(H, r2, level, pre, post, w, 3)
+    w2 = M @ z2
+    b = ratio(dots(w1, w2), n1)
+    w2 = w2 - w1 * b
+    z2 = z2 - z1 * b
+    a2 = ratio(dots(w2, r2), dots(w2, w2))
+    return z1 * a1 + z2 * a2
+
+
 def vcycle(H: Hierarchy, f: np.ndarray, level: int = 0, pre: int = 2,
            post: int = 2, w: float = 0.8, gamma: int = 1) -> np.ndarray:
     """Multigrid cycle for M_level e = f from a zero initial guess, following
     Alg. "Two-grid cycle": pre-relax, restrict the residual with P^T, solve
     the coarse problem recursively (``gamma`` = 1 gives the V-cycle, 2 the
-    W-cycle), prolong and correct, post-relax.  The coarsest level is solved
-    with the dense LU."""
+    W-cycle: two recursive calls, the second on the residual of the first; 3
+    the K-cycle of Sec. 5.3, see ``_kcycle_correction``), prolong and
+    correct, post-relax.  The coarsest level is solved with the dense LU, once
+    per visit."""
     if level == H.levels - 1:
         return H.coarse_solve(f)
     M, d, P = H.M[level], H.diag[level], H.P[level]
     u = np.zeros_like(f)
     u = jacobi(M, d, u, f, w, pre)
     rc = P.T @ (f - M @ u)
-    ec = np.zeros_like(rc)
-    for _ in range(gamma):
-        if _ == 0:
-            ec = vcycle(H, rc, level + 1, pre, post, w, gamma)
-        else:
-            Mc = H.M[level + 1]
+    Mc = H.M[level + 1]
+    if gamma == 3 and level + 1 < H.levels - 1:
+        ec = _kcycle_correction(H, rc, level + 1, pre, post, w)
+    else:
+        ec = vcycle(H, rc, level + 1, pre, post, w, min(gamma, 2))
+        if gamma == 2 and level + 1 < H.levels - 1:
             ec = ec + vcycle(H, rc - Mc @ ec, level + 1, pre, post, w, gamma)
     u = u + P @ ec
     u = jacobi(M, d, u, f, w, post)
@@ -501,16 +532,17 @@ class Solver:
         return U, infos
 
     def solve(self, Q_cols: np.ndarray, tol=1e-6, restart=10, block=None,
-              max_restarts=50):
+              max_restarts=50, gamma: int = 1):
         """Q_cols: (N, s).  Columns are solved in groups of ``block``
-        (independent block-FGMRES runs); returns (U, [info per group])."""
+        (independent block-FGMRES runs); returns (U, [info per group]).
+        ``gamma`` picks the cycle: 1 V, 2 W, 3 K."""
         N, s = Q_cols.shape
         block = s if block is None else block
         U = np.zeros_like(Q_cols, dtype=np.complex128)
         infos = []
         for g0 in range(0, s, block):
             sl = slice(g0, min(s, g0 + block))
-            U[:, sl], inf = block_fgmres(self.A, self.precond, Q_cols[:, sl],
+            U[:, sl], inf = block_fgmres(self.A, lambda V: self.precond(V, gamma), Q_cols[:, sl],
                                          tol, restart, max_restarts)
             infos.append(inf)
         return U, infos

@@ -555,3 +555,36 @@ def test_fwi_jv_jtw_dot_product():
     Am = O.helmholtz_matrix(m - eps * v.reshape(m.shape), g, omega, h)
     num = (O.dense_solve(Ap, Q) - O.dense_solve(Am, Q))[recv] / (2 * eps)
     np.testing.assert_allclose(Jv, num, rtol=1e-6, atol=1e-9 * np.abs(num).max())
+
+
+def test_kcycle_coarse_correction_minimises_the_residual():
+    """The K-cycle's coarse correction is the minimal-residual combination of
+    the two preconditioned directions: brute-force least squares over
+    span{z1, z2} gives the same residual."""
+    p = small_problem((32, 32), seed=6)
+    shape = p["m"].shape
+    M = O.helmholtz_matrix(p["m"], p["gamma"], p["omega"], p["h"], 0.5)
+    H = O.Hierarchy(M, shape, 4)
+    rng = np.random.default_rng(33)
+    r = crand(rng, H.M[1].shape[0], 2)
+    e = O._kcycle_correction(H, r, 1, 2, 2, 0.8)
+    Mc = H.M[1]
+    z1 = O.vcycle(H, r, 1, gamma=3)
+    for j in range(2):
+        r2 = r[:, j] - Mc @ (z1[:, j] * (np.vdot(Mc @ z1[:, j], r[:, j]) / np.vdot(Mc @ z1[:, j], Mc @ z1[:, j])))
+        z2 = O.vcycle(H, r2[:, None], 1, gamma=3)[:, 0]
+        Z = np.stack([z1[:, j], z2], axis=1)
+        c, *_ = np.linalg.lstsq(Mc @ Z, r[:, j], rcond=None)
+        best = np.linalg.norm(r[:, j] - Mc @ (Z @ c))
+        got = np.linalg.norm(r[:, j] - Mc @ e[:, j])
+        assert got <= best * (1 + 1e-8) + 1e-12
+
+
+def test_kcycle_fgmres_converges():
+    p = small_problem((32, 32), seed=7)
+    S = O.Solver(p["m"], p["gamma"], p["omega"], p["h"], levels=4)
+    rng = np.random.default_rng(34)
+    Q = crand(rng, S.A.shape[0], 2)
+    X, info = O.block_fgmres(S.A, lambda V: S.precond(V, 3), Q, tol=1e-10, restart=10)
+    assert info.converged
+    assert np.linalg.norm(X - O.dense_solve(S.A, Q)) <= 1e-7 * np.linalg.norm(X)
