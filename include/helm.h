@@ -99,7 +99,10 @@ typedef struct {
                                 1 = three tf32 products on hi/lo splits
                                 (FP32-class)                                    */
     int cycle_gamma;         /* 1 = V-cycle, 2 = W-cycle (two coarse visits per
-                                level, Sec. 4)                                  */
+                                level, Sec. 4), 3 = K-cycle (Sec. 5.3: each
+                                coarse system solved by two flexible Krylov
+                                steps preconditioned by the next cycle; here
+                                per column, GCR(2); FGMRES only; s <= 256)     */
     int krylov;              /* 0 = block FGMRES(restart); 1 = block BiCGSTAB
                                 (Sec. 5.3 "W-BiCG", El Guennouni et al.; needs
                                 a fixed preconditioner: not with the learned

@@ -529,6 +529,45 @@ __global__ void k_axpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, l
     if (e < n) y[e] = y[e] + ldg(x + e);
 }
 
+// K-cycle helpers: out[j] += sum_node conj(a[node][j]) b[node][j] (double
+// accumulation; s <= 256: thread t takes column t % s), and
+// y[node][j] += sign * (num_j / den_j) x[node][j].
+template <typename T>
+__global__ void __launch_bounds__(256) k_coldot(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ b,
+                                                 long long N, int s, double2* __restrict__ out) {
+    __shared__ double2 red[256];
+    const int per = 256 / s;
+    const int j = threadIdx.x % s, sub = threadIdx.x / s;
+    double re = 0.0, im = 0.0;
+    if (sub < per)
+        for (long long n = (long long)blockIdx.x * per + sub; n < N; n += (long long)gridDim.x * per) {
+            cplx<T> x = a[n * s + j], y = b[n * s + j];
+            re += (double)x.re * y.re + (double)x.im * y.im;
+            im += (double)x.re * y.im - (double)x.im * y.re;
+        }
+    red[threadIdx.x] = make_double2(sub < per ? re : 0.0, sub < per ? im : 0.0);
+    __syncthreads();
+    if (sub == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int k = 0; k < per; ++k) { tr += red[k * s + j].x; ti += red[k * s + j].y; }
+        atomicAdd(&out[j].x, tr);
+        atomicAdd(&out[j].y, ti);
+    }
+}
+
+template <typename T>
+__global__ void k_kc_axpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x,
+                          const double2* __restrict__ num, const double2* __restrict__ den,
+                          double sign, long long N, int s) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= N * s) return;
+    int j = (int)(e % s);
+    double d = den[j].x;
+    if (!(d > 0.0)) return;
+    cplx<T> c = mk<T>((T)(sign * num[j].x / d), (T)(sign * num[j].y / d));
+    y[e] = y[e] + c * x[e];
+}
+
 // ---------------- launchers ----------------
 //
 // Each launcher reports the launch's algorithmic traffic and flops to the
@@ -610,6 +649,24 @@ void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const 
         k_resid_restrict_v<T, FT, Op, 1><<<G.grid, G.block, 0, L.st>>>(op, gc, u, f, rc, s);
     else
         k_resid_restrict<T, FT, Op><<<blocks_for(total), kThreads, 0, L.st>>>(op, gc, u, f, rc, s, total);
+    L.post();
+}
+
+template <typename T>
+void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long long N, int s,
+                   double2* out) {
+    cudaMemsetAsync(out, 0, sizeof(double2) * s, L.st);
+    L.pre(KID_LAYOUT, 2.0 * N * s * cb<T>(), 8.0 * N * s);
+    long long want = (N + 255) / 256;
+    k_coldot<T><<<(unsigned)(want < 2 * 152 ? (want < 1 ? 1 : want) : 2 * 152), 256, 0, L.st>>>(a, b, N, s, out);
+    L.post();
+}
+
+template <typename T>
+void launch_kc_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, const double2* num,
+                    const double2* den, double sign, long long N, int s) {
+    L.pre(KID_LAYOUT, 3.0 * N * s * cb<T>(), 8.0 * N * s);
+    k_kc_axpy<T><<<blocks_for(N * s), kThreads, 0, L.st>>>(y, x, num, den, sign, N, s);
     L.post();
 }
 
@@ -733,6 +790,10 @@ void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count
     template void launch_prolong_add<T>(const Launch&, const Grid&, const Grid&, const cplx<T>*, \
                                         cplx<T>*, int);                                          \
     template void launch_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, long long);            \
+    template void launch_coldot<T>(const Launch&, const cplx<T>*, const cplx<T>*, long long, int, \
+                                   double2*);                                                    \
+    template void launch_kc_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, const double2*,      \
+                                    const double2*, double, long long, int);                    \
     template void launch_residual<T, GalOp<T>>(const Launch&, const GalOp<T>&, const cplx<T>*,   \
                                                const cplx<T>*, cplx<T>*, int);                   \
     template void launch_dense_apply<T>(const Launch&, const cplx<T>*, int, const cplx<T>*,      \

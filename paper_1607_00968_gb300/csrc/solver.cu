@@ -55,6 +55,8 @@ struct Level {
     void* f = nullptr;       // coarse-level right-hand side (levels >= 1)
     void* wf = nullptr;      // W-cycle: residual and correction of the second
     void* we = nullptr;      // coarse visit (levels >= 1)
+    void* kb[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // K-cycle: z1 w1 r2 z2 w2
+    double2* kd = nullptr;   // K-cycle column products (6 x s)
 };
 
 }  // namespace
@@ -259,6 +261,46 @@ void coarsest(helm_ctx* c, const cplx<T>* f, cplx<T>* u, int s) {
         helm::launch_dense_apply<T>(c->L(), c->Minv, c->nc, f, u, s);
 }
 
+template <typename T, typename FT>
+void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s);
+
+// K-cycle coarse correction on level k (Sec. 5.3 "K-cycles": two iterations
+// of a flexible Krylov method, preconditioned by level k's cycle, on the
+// coarse system), per column as GCR(2):
+//   z1 = C(r), w1 = M z1, a1 = w1^H r / w1^H w1, r2 = r - a1 w1,
+//   z2 = C(r2), w2 = M z2, b = w1^H w2 / w1^H w1, w2 -= b w1, z2 -= b z1,
+//   a2 = w2^H r2 / w2^H w2, e = a1 z1 + a2 z2.
+// The column products stay on the device (no host synchronisation).
+template <typename T>
+void kcycle_correction(helm_ctx* c, int k, const cplx<T>* r, cplx<T>* e, int s) {
+    Level& lev = c->lv[k];
+    const long long n = lev.g.N * (long long)s;
+    cplx<T>* z1 = reinterpret_cast<cplx<T>*>(lev.kb[0]);
+    cplx<T>* w1 = reinterpret_cast<cplx<T>*>(lev.kb[1]);
+    cplx<T>* r2 = reinterpret_cast<cplx<T>*>(lev.kb[2]);
+    cplx<T>* z2 = reinterpret_cast<cplx<T>*>(lev.kb[3]);
+    cplx<T>* w2 = reinterpret_cast<cplx<T>*>(lev.kb[4]);
+    double2 *d11 = lev.kd, *d1r = lev.kd + s, *d12 = lev.kd + 2 * s, *d22 = lev.kd + 3 * s,
+            *d2r = lev.kd + 4 * s;
+    helm::GalOp<T> op = gal_op<T>(c, k);
+    cycle<T, T>(c, k, r, z1, s);
+    helm::launch_apply<T, T, T, helm::GalOp<T>>(c->L(), op, z1, w1, s);
+    helm::launch_coldot<T>(c->L(), w1, w1, lev.g.N, s, d11);
+    helm::launch_coldot<T>(c->L(), w1, r, lev.g.N, s, d1r);
+    cudaMemcpyAsync(r2, r, sizeof(cplx<T>) * n, cudaMemcpyDeviceToDevice, c->st);
+    helm::launch_kc_axpy<T>(c->L(), r2, w1, d1r, d11, -1.0, lev.g.N, s);
+    cycle<T, T>(c, k, r2, z2, s);
+    helm::launch_apply<T, T, T, helm::GalOp<T>>(c->L(), op, z2, w2, s);
+    helm::launch_coldot<T>(c->L(), w1, w2, lev.g.N, s, d12);
+    helm::launch_kc_axpy<T>(c->L(), w2, w1, d12, d11, -1.0, lev.g.N, s);
+    helm::launch_kc_axpy<T>(c->L(), z2, z1, d12, d11, -1.0, lev.g.N, s);
+    helm::launch_coldot<T>(c->L(), w2, w2, lev.g.N, s, d22);
+    helm::launch_coldot<T>(c->L(), w2, r2, lev.g.N, s, d2r);
+    helm::launch_zero(c->L(), e, sizeof(cplx<T>) * n);
+    helm::launch_kc_axpy<T>(c->L(), e, z1, d1r, d11, 1.0, lev.g.N, s);
+    helm::launch_kc_axpy<T>(c->L(), e, z2, d2r, d22, 1.0, lev.g.N, s);
+}
+
 // out = cycle(f) on level l with zero initial guess.  `out` must not alias the
 // level's own work buffers.
 template <typename T, typename FT>
@@ -289,7 +331,10 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
     cplx<T>* fc = reinterpret_cast<cplx<T>*>(nxt.f);
     cplx<T>* ec = reinterpret_cast<cplx<T>*>(nxt.e);
     restrict_level<T, FT>(c, l, cur, f, fc, s);
-    cycle<T, T>(c, l + 1, fc, ec, s);
+    if (c->p.cycle_gamma == 3 && l + 1 < Lv - 1)
+        kcycle_correction<T>(c, l + 1, fc, ec, s);
+    else
+        cycle<T, T>(c, l + 1, fc, ec, s);
     if (c->p.cycle_gamma == 2 && l + 1 < Lv - 1) {
         // W-cycle (Sec. 4: two recursive calls): a second coarse visit on the
         // residual of the first, ec += cycle(fc - M_{l+1} ec)
@@ -325,6 +370,9 @@ void free_workspace(helm_ctx* c) {
     for (auto& l : c->lv) {
         dfree(l.u0); dfree(l.u1); dfree(l.e); dfree(l.f); dfree(l.wf); dfree(l.we);
         l.u0 = l.u1 = l.e = l.f = l.wf = l.we = nullptr;
+        for (auto& q : l.kb) { dfree(q); q = nullptr; }
+        dfree(l.kd);
+        l.kd = nullptr;
     }
     dfree(c->V); dfree(c->Z); dfree(c->W); dfree(c->W2); dfree(c->Bint); dfree(c->X);
     dfree(c->R); dfree(c->abi_in); dfree(c->abi_out); dfree(c->partial); dfree(c->small);
@@ -349,6 +397,8 @@ void free_workspace(helm_ctx* c) {
 }
 
 helm_status ensure_workspace(helm_ctx* c, int s) {
+    if (c->p.cycle_gamma == 3 && s > 256)
+        return fail(c, HELM_ERR_ARG, "the K-cycle takes at most 256 columns per block");
     if (s <= c->s_cap) return HELM_OK;
     free_workspace(c);
     const long long N = c->N();
@@ -364,6 +414,10 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
             if (c->p.cycle_gamma == 2) {
                 CUDA_TRY(c, dalloc(&c->lv[l].wf, b));
                 CUDA_TRY(c, dalloc(&c->lv[l].we, b));
+            }
+            if (c->p.cycle_gamma == 3) {
+                for (int q = 0; q < 5; ++q) CUDA_TRY(c, dalloc(&c->lv[l].kb[q], b));
+                CUDA_TRY(c, dalloc(&c->lv[l].kd, sizeof(double2) * 6 * (size_t)s));
             }
         }
     }
@@ -1154,8 +1208,10 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         return fail(nullptr, HELM_ERR_ARG, "bad precision policy");
     if (p->prec == HELM_MIXED_C64_LEARNED && (p->dim != 2 || !p->learned_weights))
         return fail(nullptr, HELM_ERR_ARG, "the learned stage needs a 2D grid and learned_weights");
-    if ((p->cycle_gamma != 1 && p->cycle_gamma != 2) || (p->krylov != 0 && p->krylov != 1))
-        return fail(nullptr, HELM_ERR_ARG, "cycle_gamma must be 1 or 2, krylov 0 or 1");
+    if (p->cycle_gamma < 1 || p->cycle_gamma > 3 || (p->krylov != 0 && p->krylov != 1))
+        return fail(nullptr, HELM_ERR_ARG, "cycle_gamma must be 1, 2 or 3, krylov 0 or 1");
+    if (p->krylov == 1 && p->cycle_gamma == 3)
+        return fail(nullptr, HELM_ERR_ARG, "the K-cycle is nonlinear: use it with FGMRES (krylov 0)");
     if (p->krylov == 1 && p->prec == HELM_MIXED_C64_LEARNED)
         return fail(nullptr, HELM_ERR_ARG, "block BiCGSTAB needs a fixed preconditioner (no learned stage)");
     if (p->krylov == 1 && p->prec == HELM_MIXED_C64 && p->block > 2)

@@ -197,7 +197,7 @@ class Solver:
         p.restart, p.block, p.max_restarts = int(restart), int(block), int(max_restarts)
         p.prec = PREC[prec]
         p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
-        p.cycle_gamma = {"V": 1, "W": 2}[cycle]
+        p.cycle_gamma = {"V": 1, "W": 2, "K": 3}[cycle]
         p.krylov = {"fgmres": 0, "bicgstab": 1}[krylov]
         self.learned_weights = learned_weights        # keeps the blob alive
         p.learned_weights = _ptr(learned_weights) if learned_weights is not None else None

@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--nsrc", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cycle", default="V", choices=["V", "W", "K"])
+    ap.add_argument("--krylov", default="fgmres", choices=["fgmres", "bicgstab"])
     args = ap.parse_args()
 
     import torch
@@ -39,7 +41,8 @@ def main():
     else:
         P = inputs.layered3d_problem(seed=args.seed, freq_hz=args.freq)
     S = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, levels=args.levels,
-                    block=args.block, restart=args.restart, prec=args.prec, max_restarts=200)
+                    block=args.block, restart=args.restart, prec=args.prec, max_restarts=200,
+                    cycle=args.cycle, krylov=args.krylov)
     Q = torch.as_tensor(P.rhs()[: args.nsrc]).cuda()
     S.solve(Q, args.tol)          # warm-up on the full block (same launch shapes)
     S.profile(True)
@@ -50,6 +53,7 @@ def main():
     dt = time.perf_counter() - t0
     prof = {k: v for k, v in S.profile_read().items() if v["launches"]}
     print(json.dumps({"workload": P.name, "freq_hz": args.freq, "prec": args.prec,
+                      "cycle": args.cycle, "krylov": args.krylov, "block": args.block,
                       "seconds": dt, "rhs_per_s": Q.shape[0] / dt,
                       "cycles": int(info.iters.max()), "max_relres": float(info.relres.max()),
                       "kernels": prof}))

@@ -338,6 +338,48 @@ def test_wcycle_matches_oracle(H, cells, levels):
     assert rel(z32, O.vcycle(Hh, f, gamma=2)) < 5e-3
 
 
+# --------------------------------------------------------------------------
+# K-cycle (Sec. 5.3 "K-cycles")
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("cells,levels", [((40, 24), 4), ((16, 12, 8), 3)])
+def test_kcycle_matches_oracle(H, cells, levels):
+    m, g, h, om = layered(cells)
+    S = H.Solver(m, g, h, om, levels=levels, cycle="K")
+    Hh = O.Hierarchy(O.helmholtz_matrix(m, g, om, h, 0.5), m.shape, levels)
+    rng = np.random.default_rng(41)
+    f = crand(rng, S.N, 6)
+    ref = O.vcycle(Hh, f, gamma=3)
+    z = S.vcycle(dev(f), "c128").cpu().numpy()
+    assert rel(z, ref) < 1e-11
+    z32 = S.vcycle(dev(f), "c64").cpu().numpy()
+    assert rel(z32, ref) < 5e-3
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_kcycle_fgmres_matches_oracle(H, prec):
+    cells, levels, s = (64, 32), 4, 5
+    m, g, h, om = layered(cells, width=6)
+    S = H.Solver(m, g, h, om, levels=levels, block=5, prec=prec, cycle="K", restart=10)
+    So = O.Solver(m, g, om, h, levels=levels)
+    Q = I.point_sources(m.shape, I.line_positions(m.shape, s, 2, 6), h)
+    U, info, st = S.solve(dev(Q), tol=1e-10)
+    assert st == 0
+    U = U.cpu().numpy()
+    assert np.all(O.relres(So.A, U.T, Q.T) <= 1e-10)
+    Uo, infos = So.solve(Q.T.copy(), tol=1e-10, gamma=3)
+    for k in range(s):
+        assert rel(U[k], Uo[:, k]) <= 1e-6
+    if prec == "c128":
+        assert abs(int(info.iters.max()) - infos[0].iters) <= 2, (info.iters, infos[0].iters)
+
+
+def test_kcycle_rejects_bicgstab(H):
+    m, g, h, om = layered((32, 16))
+    with pytest.raises(RuntimeError):
+        H.Solver(m, g, h, om, levels=3, cycle="K", krylov="bicgstab")
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("cells,levels,s,block", [((64, 32), 3, 6, 3), ((16, 16, 8), 3, 4, 4)])
 def test_bicgstab_matches_oracle(H, prec, cells, levels, s, block):
