@@ -112,6 +112,15 @@ typedef struct {
                                 complex128 cycle converges at any block);
                                 iterations capped at restart * max_restarts
                                 per run, max_restarts + 1 runs                  */
+    int graphs;              /* block FGMRES without the learned stage: replay
+                                each Krylov step's device work (cycle, A Z_j,
+                                Gram-Schmidt, first QR Gram and their copies
+                                to the host) from a CUDA graph captured on the
+                                step's first use. 0 = launch directly,
+                                1 = always, 2 = when N * s <= 4,194,304
+                                (launch-bound sizes).  Never while the
+                                profiler is on (it times single launches).
+                                Results are identical either way.            */
 } helm_params;
 
 typedef struct {
@@ -124,7 +133,7 @@ typedef struct {
 
 /* Fill p with the defaults of Sec. 5.3 (levels 3, V(2,2), weight 0.8,
    restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128,
-   coarse_tf32x3 0, cycle_gamma 1, krylov 0. */
+   coarse_tf32x3 0, cycle_gamma 1, krylov 0, graphs 2. */
 void helm_default_params(helm_params* p);
 
 /* Set up the hierarchy for one (m, gamma, omega) (Sec. 4: set-up once, reused

@@ -10,6 +10,9 @@ namespace helm {
 // y = Op x  (T: arithmetic precision; U: input element; V: output element)
 template <typename T, typename U, typename V, typename Op>
 void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, int s);
+// y = A x on the fine grid in FP64 arithmetic, x complex64, y written as an
+// FMT_DD block (two complex64 planes of N*s, hi then lo; needs s <= 512)
+void launch_apply_dd(const Launch& L, const FineOp<double>& op, const c64* x, c64* y, int s);
 
 // r = b - Op x
 template <typename T, typename Op>
@@ -152,12 +155,26 @@ void launch_to_internal(const Launch& L, const c128* abi, c128* internal, long l
 void launch_from_internal(const Launch& L, const c128* internal, c128* abi, long long N, int s,
                           bool conjugate);
 
+// Storage formats of a block of N*s complex values for the double-float
+// Krylov kernels: FMT_C128 complex128; FMT_DD an unevaluated float pair per
+// component in two complex64 planes (hi at [0, N*s), lo at [N*s, 2*N*s) in
+// complex64 units: 16 bytes per value, like complex128); FMT_C64 complex64.
+enum : int { FMT_C128 = 0, FMT_DD = 1, FMT_C64 = 2 };
+// true when the double-float Gram and combination kernels cover (s, sb), the
+// condition for keeping a Krylov basis in FMT_DD
+bool dd_formats_ok(int s, int sb);
+
 // Block Gram per group:  out[i][g][a][b] = sum_node conj(X_i[node][g*sb+a]) Y[node][g*sb+b]
 // for i < nb (X_i = X + i*xstride).  partial: scratch of gram_partial_elems().
 long long gram_partial_elems(long long N, int nb, int s, int sb);
 // emulate: double-float arithmetic on the FP32 pipes instead of FP64.
 void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
                  long long N, int s, int sb, c128* partial, c128* out, bool emulate);
+
+// Same with the operands' formats (xstride in elements of X's format: 16
+// bytes for FMT_C128 and FMT_DD, 8 for FMT_C64).  FMT_DD needs emulate.
+void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xstride, const void* Y,
+                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate);
 
 // out[node][g*sb+b] = beta*out + sign * sum_{i<nb} sum_a X_i[node][g*sb+a] C[i][g][a][b]
 // emulate: double-float arithmetic (needs csplit: scratch of nb*G*sb*sb float4
@@ -166,6 +183,12 @@ template <typename TX>
 void launch_combine(const Launch& L, c128* out, double beta, double sign, const cplx<TX>* X,
                     int nb, long long xstride, const c128* C, long long N, int s, int sb,
                     bool emulate, float4* csplit);
+
+// Same with formats; an FMT_DD output or X needs emulate and
+// dd_formats_ok(s, sb), and an FMT_DD output beta in {0, 1}, sign = +-1.
+void launch_combine_f(const Launch& L, void* out, int of, double beta, double sign, const void* X,
+                      int xf, int nb, long long xstride, const c128* C, long long N, int s, int sb,
+                      bool emulate, float4* csplit);
 
 // per-column squared 2-norms of X (N x s node-major): out[j] (FP64)
 long long colnorm_partial_elems(long long N, int s);
@@ -176,6 +199,8 @@ void launch_colnorm2(const Launch& L, const c128* X, long long N, int s, double*
 // columns with mask[j] != 0; other columns untouched.
 void launch_fill_random(const Launch& L, c128* X, long long N, int s, const int* mask,
                         unsigned long long seed);
+void launch_fill_random_f(const Launch& L, void* X, int of, long long N, int s, const int* mask,
+                          unsigned long long seed);
 
 void launch_zero(const Launch& L, void* p, size_t bytes);
 

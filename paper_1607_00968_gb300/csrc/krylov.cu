@@ -160,6 +160,42 @@ __device__ __forceinline__ float4 split_c(c128 v) {
     return r;
 }
 
+// Operand formats of the double-float kernels (FMT_* in kernels.h).  A block
+// of N*s complex values is either complex128 (split into float pairs as it is
+// staged), two complex64 planes holding an unevaluated pair hi + lo (hi at
+// [0, N*s), lo at [N*s, 2*N*s): already split, same 16 bytes per value), or
+// complex64 (lo = 0).  ld() reads element e of a block at byte address b.
+template <int F> struct DDIn;
+template <> struct DDIn<FMT_C128> {
+    using Raw = c128;
+    __device__ static Raw ld(const char* b, long long, long long e) { return reinterpret_cast<const c128*>(b)[e]; }
+    __device__ static float4 f4(const Raw& r) { return split_c(r); }
+};
+template <> struct DDIn<FMT_DD> {
+    using Raw = float4;
+    __device__ static Raw ld(const char* b, long long plane, long long e) {
+        const float2* p = reinterpret_cast<const float2*>(b);
+        float2 h = p[e], l = p[plane + e];
+        return make_float4(h.x, l.x, h.y, l.y);
+    }
+    __device__ static float4 f4(const Raw& r) { return r; }
+};
+template <> struct DDIn<FMT_C64> {
+    using Raw = c64;
+    __device__ static Raw ld(const char* b, long long, long long e) { return reinterpret_cast<const c64*>(b)[e]; }
+    __device__ static float4 f4(const Raw& r) { return split_c(r); }
+};
+
+__host__ __device__ constexpr long long fmt_bytes(int f) { return f == FMT_C64 ? 8 : 16; }
+
+// error-free sum: a + b = s + e exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
 // (S, L) += (ah + al) * (bh + bl)
 __device__ __forceinline__ void dd_mac(float& S, float& L, float ah, float al, float bh, float bl) {
     float p = __fmul_rn(ah, bh);
@@ -181,9 +217,9 @@ constexpr int kMaxQPT = 4;   // quads per thread; a quad is one row a and four c
 // that layout share the CTA and take every R-th node of a tile, and their
 // sums are added at the end.  The next node tile is loaded into registers
 // while the current one is being used.
-template <int QPT>
-__global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X, long long xstride,
-                                                       const c128* __restrict__ Y, long long N,
+template <int QPT, int XF, int YF>
+__global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X, long long xstride,
+                                                       const char* __restrict__ Y, long long N,
                                                        int s, int sb, int chunks,
                                                        c128* __restrict__ partial) {
     constexpr int qpt = QPT;
@@ -202,7 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X
     const int rep = threadIdx.x / nthr;
     const int qt = threadIdx.x - rep * nthr;
     const bool active = rep < R;
-    const c128* Xi = X + (long long)i * xstride;
+    const char* Xi = X + (long long)i * xstride;     // xstride in bytes
+    const long long plane = N * s;
     long long per = (N + chunks - 1) / chunks;
     long long n0 = (long long)blockIdx.x * per;
     long long n1 = n0 + per < N ? n0 + per : N;
@@ -230,14 +267,15 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X
     }
     // register prefetch of one tile: kGramTileElems / kThreads values per operand
     constexpr int kPF = kGramTileElems / kThreads;
-    c128 px[kPF], py[kPF];
+    typename DDIn<XF>::Raw px[kPF];
+    typename DDIn<YF>::Raw py[kPF];
     auto fetch = [&](long long t0, int cnt) {
 #pragma unroll
         for (int k = 0; k < kPF; ++k) {
             int idx = threadIdx.x + k * kThreads;
             if (idx < cnt * s) {
-                px[k] = Xi[t0 * s + idx];
-                py[k] = Y[t0 * s + idx];
+                px[k] = DDIn<XF>::ld(Xi, plane, t0 * s + idx);
+                py[k] = DDIn<YF>::ld(Y, plane, t0 * s + idx);
             }
         }
     };
@@ -250,8 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const c128* __restrict__ X
         for (int k = 0; k < kPF; ++k) {
             int idx = threadIdx.x + k * kThreads;
             if (idx < cnt * s) {
-                xs[idx] = split_c(px[k]);
-                ys[idx] = split_c(py[k]);
+                xs[idx] = DDIn<XF>::f4(px[k]);
+                ys[idx] = DDIn<YF>::f4(py[k]);
             }
         }
         __syncthreads();
@@ -325,9 +363,9 @@ __global__ void k_split(const c128* __restrict__ C, float4* __restrict__ Cs, lon
 // nodes.  For each block i the tile of X_i is split into float pairs in
 // shared memory once (the tile of X_{i+1} is loaded into registers
 // meanwhile) and C_i, split beforehand by k_split, is staged beside it.
-template <typename TX>
-__global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out, double beta,
-                                                          double sign, const cplx<TX>* __restrict__ X,
+template <int XF, int OF>
+__global__ void __launch_bounds__(kThreads) k_combine_dd(char* __restrict__ out, double beta,
+                                                          double sign, const char* __restrict__ X,
                                                           int nb, long long xstride,
                                                           const float4* __restrict__ Cs, long long N,
                                                           int s, int sb) {
@@ -350,13 +388,13 @@ __global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out,
         float S[kCombineRows][2], Lc[kCombineRows][2];
 #pragma unroll
         for (int r = 0; r < kCombineRows; ++r) S[r][0] = S[r][1] = Lc[r][0] = Lc[r][1] = 0.f;
-        cplx<TX> px[kCombineRows];
+        typename DDIn<XF>::Raw px[kCombineRows];
         auto fetch = [&](int i) {
-            const cplx<TX>* Xi = X + (long long)i * xstride + t0 * s;
+            const char* Xi = X + (long long)i * xstride;   // xstride in bytes
 #pragma unroll
             for (int k = 0; k < kCombineRows; ++k) {
                 int idx = threadIdx.x + k * kThreads;
-                if (idx < cnt * s) px[k] = Xi[idx];
+                if (idx < cnt * s) px[k] = DDIn<XF>::ld(Xi, N * s, t0 * s + idx);
             }
         };
         fetch(0);
@@ -365,7 +403,7 @@ __global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out,
 #pragma unroll
             for (int k = 0; k < kCombineRows; ++k) {
                 int idx = threadIdx.x + k * kThreads;
-                if (idx < cnt * s) xs[idx] = split_c(px[k]);
+                if (idx < cnt * s) xs[idx] = DDIn<XF>::f4(px[k]);
             }
             const float4* Ci = Cs + (long long)i * csz;
             for (int idx = threadIdx.x; idx < csz; idx += kThreads) cs[idx] = Ci[idx];
@@ -395,15 +433,38 @@ __global__ void __launch_bounds__(kThreads) k_combine_dd(c128* __restrict__ out,
             int n = sub + r * per;
             if (n >= cnt) break;
             long long e = (t0 + n) * s + col;
-            double are = f2d_bits(S[r][0]) + f2d_bits(Lc[r][0]);
-            double aim = f2d_bits(S[r][1]) + f2d_bits(Lc[r][1]);
-            // beta is 0 or 1 and sign +-1 on every call of the driver; the
-            // general form costs FP64 multiplies only otherwise
-            if (sign == -1.0) { are = -are; aim = -aim; }
-            else if (sign != 1.0) { are *= sign; aim *= sign; }
-            if (beta == 1.0) { c128 o = out[e]; are += o.re; aim += o.im; }
-            else if (beta != 0.0) { c128 o = out[e]; are += beta * o.re; aim += beta * o.im; }
-            out[e] = mk(are, aim);
+            if constexpr (OF == FMT_DD) {
+                // beta in {0, 1}, sign = +-1 (checked by the launcher): the
+                // result stays an unevaluated pair, renormalised by TwoSum
+                float2* o = reinterpret_cast<float2*>(out);
+                const long long plane = N * s;
+                float h[2], l[2];
+                float2 oh = beta != 0.0 ? o[e] : make_float2(0.f, 0.f);
+                float2 ol = beta != 0.0 ? o[plane + e] : make_float2(0.f, 0.f);
+                const float ohc[2] = {oh.x, oh.y}, olc[2] = {ol.x, ol.y};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float sS = sign < 0.0 ? -S[r][q] : S[r][q];
+                    float sL = sign < 0.0 ? -Lc[r][q] : Lc[r][q];
+                    float t, err;
+                    two_sum(ohc[q], sS, t, err);
+                    err = __fadd_rn(err, __fadd_rn(olc[q], sL));
+                    two_sum(t, err, h[q], l[q]);
+                }
+                o[e] = make_float2(h[0], h[1]);
+                o[plane + e] = make_float2(l[0], l[1]);
+            } else {
+                c128* o = reinterpret_cast<c128*>(out);
+                double are = f2d_bits(S[r][0]) + f2d_bits(Lc[r][0]);
+                double aim = f2d_bits(S[r][1]) + f2d_bits(Lc[r][1]);
+                // beta is 0 or 1 and sign +-1 on every call of the driver; the
+                // general form costs FP64 multiplies only otherwise
+                if (sign == -1.0) { are = -are; aim = -aim; }
+                else if (sign != 1.0) { are *= sign; aim *= sign; }
+                if (beta == 1.0) { c128 v = o[e]; are += v.re; aim += v.im; }
+                else if (beta != 0.0) { c128 v = o[e]; are += beta * v.re; aim += beta * v.im; }
+                o[e] = mk(are, aim);
+            }
         }
     }
 }
@@ -463,7 +524,8 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     return x ^ (x >> 31);
 }
 
-__global__ void k_fill_random(c128* X, long long N, int s, const int* __restrict__ mask,
+template <int OF>
+__global__ void k_fill_random(char* Xb, long long N, int s, const int* __restrict__ mask,
                               unsigned long long seed) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= N * s) return;
@@ -473,7 +535,16 @@ __global__ void k_fill_random(c128* X, long long N, int s, const int* __restrict
     unsigned long long h2 = splitmix64(seed ^ (2ULL * (unsigned long long)e + 1ULL));
     double u1 = (double)(h1 >> 11) * (1.0 / 9007199254740992.0) - 0.5;
     double u2 = (double)(h2 >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-    X[e] = mk(u1, u2);
+    if constexpr (OF == FMT_DD) {
+        float2* X = reinterpret_cast<float2*>(Xb);
+        float h1f, l1f, h2f, l2f;
+        split_d(u1, h1f, l1f);
+        split_d(u2, h2f, l2f);
+        X[e] = make_float2(h1f, h2f);
+        X[N * s + e] = make_float2(l1f, l2f);
+    } else {
+        reinterpret_cast<c128*>(Xb)[e] = mk(u1, u2);
+    }
 }
 
 }  // namespace
@@ -484,41 +555,10 @@ long long gram_partial_elems(long long N, int nb, int s, int sb) {
     return (long long)gram_chunks(N, nb, s) * nb * E1;
 }
 
-void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
-                 long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
-    int G = (s + sb - 1) / sb;
-    long long E1 = (long long)G * sb * sb;
-    int chunks = gram_chunks(N, nb, s);
-    size_t smem = 2 * sizeof(c128) * (size_t)gram_tile_nodes(s) * s;
-    dim3 grid(chunks, nb);
-    L.pre(emulate ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
-    if (emulate) {
-        const int nbq = (sb + 3) / 4;
-        const long long Q = (long long)G * sb * nbq;
-        int qpt = (int)((Q + kThreads - 1) / kThreads);
-        if (qpt < 1) qpt = 1;
-        if (qpt > kMaxQPT) {
-            // more quads than one CTA holds: fall back to the FP64 kernel
-            k_gram<<<grid, kThreads, smem, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
-        } else {
-            int nthr = (int)((Q + qpt - 1) / qpt);
-            int R = kThreads / nthr;
-            size_t red = R > 1 ? (size_t)R * E1 * sizeof(double2) : 0;
-            size_t sm2 = smem > red ? smem : red;
-            if (qpt == 3) qpt = 4;
-            auto kern = qpt == 1 ? k_gram_dd<1> : (qpt == 2 ? k_gram_dd<2> : k_gram_dd<4>);
-            if (sm2 > 48 * 1024)
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-            kern<<<grid, kThreads, sm2, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
-        }
-    }
-    else
-        k_gram<<<grid, kThreads, smem, L.st>>>(X, xstride, Y, N, s, sb, chunks, partial);
-    L.post();
-    long long E = E1 * nb;
-    L.pre(KID_GRAM_REDUCE, (chunks + 1.0) * E * 16.0, 2.0 * chunks * E);
-    k_gram_reduce<<<(unsigned)((E + 31) / 32), 256, 0, L.st>>>(partial, chunks, E, out);
-    L.post();
+bool gram_dd_ok(int s, int sb) {
+    const int G = (s + sb - 1) / sb;
+    const long long Q = (long long)G * sb * ((sb + 3) / 4);
+    return (Q + kThreads - 1) / kThreads <= kMaxQPT;
 }
 
 bool combine_dd_ok(int s, int sb) {
@@ -526,38 +566,128 @@ bool combine_dd_ok(int s, int sb) {
                                     sizeof(float4) <= 160 * 1024;
 }
 
+bool dd_formats_ok(int s, int sb) { return gram_dd_ok(s, sb) && combine_dd_ok(s, sb); }
+
+namespace {
+template <int QPT>
+void gram_dd_dispatch(int xf, int yf, dim3 grid, size_t sm, cudaStream_t st, const char* X,
+                      long long xs, const char* Y, long long N, int s, int sb, int chunks,
+                      c128* partial) {
+    auto pick = [&](auto kern) {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<grid, kThreads, sm, st>>>(X, xs, Y, N, s, sb, chunks, partial);
+    };
+    if (xf == FMT_DD && yf == FMT_DD) pick(k_gram_dd<QPT, FMT_DD, FMT_DD>);
+    else if (xf == FMT_DD) pick(k_gram_dd<QPT, FMT_DD, FMT_C128>);
+    else if (yf == FMT_DD) pick(k_gram_dd<QPT, FMT_C128, FMT_DD>);
+    else pick(k_gram_dd<QPT, FMT_C128, FMT_C128>);
+}
+}  // namespace
+
+void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xstride, const void* Y,
+                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
+    int G = (s + sb - 1) / sb;
+    long long E1 = (long long)G * sb * sb;
+    int chunks = gram_chunks(N, nb, s);
+    size_t smem = 2 * sizeof(c128) * (size_t)gram_tile_nodes(s) * s;
+    dim3 grid(chunks, nb);
+    const bool dd = emulate && gram_dd_ok(s, sb);
+    L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
+    if (dd) {
+        const int nbq = (sb + 3) / 4;
+        const long long Q = (long long)G * sb * nbq;
+        int qpt = (int)((Q + kThreads - 1) / kThreads);
+        if (qpt < 1) qpt = 1;
+        int nthr = (int)((Q + qpt - 1) / qpt);
+        int R = kThreads / nthr;
+        size_t red = R > 1 ? (size_t)R * E1 * sizeof(double2) : 0;
+        size_t sm2 = smem > red ? smem : red;
+        const char* Xb = static_cast<const char*>(X);
+        const char* Yb = static_cast<const char*>(Y);
+        const long long xsb = xstride * fmt_bytes(xf);
+        if (qpt == 1) gram_dd_dispatch<1>(xf, yf, grid, sm2, L.st, Xb, xsb, Yb, N, s, sb, chunks, partial);
+        else if (qpt == 2) gram_dd_dispatch<2>(xf, yf, grid, sm2, L.st, Xb, xsb, Yb, N, s, sb, chunks, partial);
+        else gram_dd_dispatch<4>(xf, yf, grid, sm2, L.st, Xb, xsb, Yb, N, s, sb, chunks, partial);
+    } else {
+        // FP64 kernel (complex128 operands only; more quads than one CTA of
+        // the double-float kernel holds falls back here too)
+        k_gram<<<grid, kThreads, smem, L.st>>>(static_cast<const c128*>(X), xstride,
+                                              static_cast<const c128*>(Y), N, s, sb, chunks, partial);
+    }
+    L.post();
+    long long E = E1 * nb;
+    L.pre(KID_GRAM_REDUCE, (chunks + 1.0) * E * 16.0, 2.0 * chunks * E);
+    k_gram_reduce<<<(unsigned)((E + 31) / 32), 256, 0, L.st>>>(partial, chunks, E, out);
+    L.post();
+}
+
+void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
+                 long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
+    launch_gram_f(L, X, FMT_C128, nb, xstride, Y, FMT_C128, N, s, sb, partial, out, emulate);
+}
+
+namespace {
+template <int XF, int OF>
+void combine_dd_go(const Launch& L, int grid, size_t smem, void* out, double beta, double sign,
+                   const void* X, int nb, long long xstride_bytes, const float4* cs, long long N,
+                   int s, int sb) {
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_combine_dd<XF, OF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_combine_dd<XF, OF><<<grid, kThreads, smem, L.st>>>(static_cast<char*>(out), beta, sign,
+                                                          static_cast<const char*>(X), nb,
+                                                          xstride_bytes, cs, N, s, sb);
+}
+}  // namespace
+
+void launch_combine_f(const Launch& L, void* out, int of, double beta, double sign, const void* X,
+                      int xf, int nb, long long xstride, const c128* C, long long N, int s, int sb,
+                      bool emulate, float4* csplit) {
+    const double xb = xf == FMT_C64 ? 8.0 : 16.0;
+    if (emulate && csplit && combine_dd_ok(s, sb)) {
+        const int T = (kThreads / s) * kCombineRows;
+        const int G = (s + sb - 1) / sb;
+        size_t smem = (size_t)(T * s + G * sb * sb) * sizeof(float4);
+        long long ntiles = (N + T - 1) / T;
+        int grid = (int)(ntiles < 4LL * 152 * 4 ? ntiles : 4LL * 152 * 4);
+        long long nc = (long long)nb * G * sb * sb;
+        L.pre(KID_LAYOUT, 32.0 * nc, 0);
+        k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
+        L.post();
+        L.pre(KID_COMBINE_DD, (double)N * s * (nb * xb + (beta != 0.0 ? 32.0 : 16.0)),
+              8.0 * nb * (double)N * s * sb);
+        const long long xsb = xstride * fmt_bytes(xf);
+        if (of == FMT_DD) {
+            if (xf == FMT_DD) combine_dd_go<FMT_DD, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+            else if (xf == FMT_C64) combine_dd_go<FMT_C64, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+            else combine_dd_go<FMT_C128, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+        } else {
+            if (xf == FMT_DD) combine_dd_go<FMT_DD, FMT_C128>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+            else if (xf == FMT_C64) combine_dd_go<FMT_C64, FMT_C128>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+            else combine_dd_go<FMT_C128, FMT_C128>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
+        }
+        L.post();
+        return;
+    }
+    // FP64 kernel: complex128 output, complex128 or complex64 X
+    L.pre(KID_COMBINE, (double)N * s * (nb * xb + (beta != 0.0 ? 32.0 : 16.0)),
+          8.0 * nb * (double)N * s * sb);
+    if (xf == FMT_C64)
+        k_combine<float><<<blocks_for(N * s), kThreads, 0, L.st>>>(static_cast<c128*>(out), beta, sign,
+                                                                    static_cast<const c64*>(X), nb,
+                                                                    xstride, C, N, s, sb);
+    else
+        k_combine<double><<<blocks_for(N * s), kThreads, 0, L.st>>>(static_cast<c128*>(out), beta, sign,
+                                                                     static_cast<const c128*>(X), nb,
+                                                                     xstride, C, N, s, sb);
+    L.post();
+}
+
 template <typename TX>
 void launch_combine(const Launch& L, c128* out, double beta, double sign, const cplx<TX>* X,
                     int nb, long long xstride, const c128* C, long long N, int s, int sb,
                     bool emulate, float4* csplit) {
-    {
-        if (emulate && csplit && combine_dd_ok(s, sb)) {
-            const int T = (kThreads / s) * kCombineRows;
-            const int G = (s + sb - 1) / sb;
-            size_t smem = (size_t)(T * s + G * sb * sb) * sizeof(float4);
-            long long ntiles = (N + T - 1) / T;
-            int grid = (int)(ntiles < 4LL * 152 * 4 ? ntiles : 4LL * 152 * 4);
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k_combine_dd<TX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            long long nc = (long long)nb * G * sb * sb;
-            L.pre(KID_LAYOUT, 32.0 * nc, 0);
-            k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
-            L.post();
-            L.pre(KID_COMBINE_DD,
-                  (double)N * s * (nb * 2.0 * sizeof(TX) + (beta != 0.0 ? 32.0 : 16.0)),
-                  8.0 * nb * (double)N * s * sb);
-            k_combine_dd<TX><<<grid, kThreads, smem, L.st>>>(out, beta, sign, X, nb, xstride, csplit,
-                                                             N, s, sb);
-            L.post();
-            return;
-        }
-    }
-    L.pre(KID_COMBINE, (double)N * s * (nb * 2.0 * sizeof(TX) + (beta != 0.0 ? 32.0 : 16.0)),
-          8.0 * nb * (double)N * s * sb);
-    k_combine<TX><<<blocks_for(N * s), kThreads, 0, L.st>>>(out, beta, sign, X, nb, xstride, C, N,
-                                                            s, sb);
-    L.post();
+    launch_combine_f(L, out, FMT_C128, beta, sign, X, sizeof(TX) == 4 ? FMT_C64 : FMT_C128, nb, xstride,
+                     C, N, s, sb, emulate, csplit);
 }
 template void launch_combine<double>(const Launch&, c128*, double, double, const c128*, int,
                                      long long, const c128*, long long, int, int, bool, float4*);
@@ -590,11 +720,19 @@ void launch_from_internal(const Launch& L, const c128* internal, c128* abi, long
     L.post();
 }
 
+void launch_fill_random_f(const Launch& L, void* X, int of, long long N, int s, const int* mask,
+                          unsigned long long seed) {
+    L.pre(KID_RANDOM, 16.0 * N * s, 0);
+    if (of == FMT_DD)
+        k_fill_random<FMT_DD><<<blocks_for(N * s), kThreads, 0, L.st>>>(static_cast<char*>(X), N, s, mask, seed);
+    else
+        k_fill_random<FMT_C128><<<blocks_for(N * s), kThreads, 0, L.st>>>(static_cast<char*>(X), N, s, mask, seed);
+    L.post();
+}
+
 void launch_fill_random(const Launch& L, c128* X, long long N, int s, const int* mask,
                         unsigned long long seed) {
-    L.pre(KID_RANDOM, 16.0 * N * s, 0);
-    k_fill_random<<<blocks_for(N * s), kThreads, 0, L.st>>>(X, N, s, mask, seed);
-    L.post();
+    launch_fill_random_f(L, X, FMT_C128, N, s, mask, seed);
 }
 
 void launch_zero(const Launch& L, void* p, size_t bytes) { cudaMemsetAsync(p, 0, bytes, L.st); }

@@ -190,6 +190,24 @@ __global__ void __launch_bounds__(256) k_apply_v(Op op, const cplx<U>* __restric
     stR<V, R>(yout + e0, w);
 }
 
+// FP64 apply with the result split into an unevaluated float pair per
+// component (hi plane at y, lo plane at y + N*s)
+template <int R>
+__global__ void __launch_bounds__(256) k_apply_dd(FineOp<double> op, const c64* __restrict__ xin,
+                                                   c64* __restrict__ yout, int s) {
+    VGEO_PROLOGUE(op.g)
+    c128 o[R];
+    op.template applyR<R>(xin, node, x, y, z, s, r0, o);
+    CV<float, R> hi, lo;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        split_d(o[k].re, hi.v[k].re, lo.v[k].re);
+        split_d(o[k].im, hi.v[k].im, lo.v[k].im);
+    }
+    stR<float, R>(yout + e0, hi);
+    stR<float, R>(yout + op.g.N * s + e0, lo);
+}
+
 template <typename T, typename FT, typename Op, int R>
 __global__ void __launch_bounds__(256) k_jacobi_v(Op op, const cplx<T>* __restrict__ uin,
                                                    const cplx<FT>* __restrict__ f,
@@ -589,6 +607,16 @@ template <typename T> struct OpCost<GalOp<T>> {
     static double flops(const GalOp<T>& op) { return 8.0 * K(op); }
     static constexpr bool fine = false;
 };
+
+void launch_apply_dd(const Launch& L, const FineOp<double>& op, const c64* x, c64* y, int s) {
+    long long total = op.g.N * s;
+    L.pre(KID_APPLY_FINE, total * (8.0 + 16.0) + op.g.N * OpCost<FineOp<double>>::coef_bytes(op),
+          total * OpCost<FineOp<double>>::flops(op));
+    Geo G = geo_for(op.g, s);
+    if (G.R == 2) k_apply_dd<2><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
+    else k_apply_dd<1><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
+    L.post();
+}
 
 template <typename T, typename U, typename V, typename Op>
 void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, int s) {

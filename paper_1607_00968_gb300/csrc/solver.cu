@@ -171,6 +171,16 @@ struct helm_ctx {
     c128* hsmall = nullptr;  // pinned host mirror of `small`
     unsigned long long rng_counter = 0x5eed;
     helm::Profiler* prof = nullptr;
+    // CUDA graphs of the FGMRES step (one per (s, j)), captured on a private
+    // stream and replayed on `st`; they hold workspace pointers, so they are
+    // destroyed with the workspace
+    struct StepGraph { int s, j; cudaGraphExec_t exec; long long launches; };
+    std::vector<StepGraph> graphs;
+    cudaStream_t cap_st = nullptr;
+    // storage format of the FGMRES basis V, W and W2 during a solve:
+    // helm::FMT_DD (unevaluated float pairs) on the complex64 path when the
+    // double-float kernels cover the block shape, else complex128
+    int kfmt = 0;
 
     Launch L() { return Launch{st, &launches, prof}; }
     long long N() const { return lv[0].g.N; }
@@ -367,6 +377,8 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
 // ---------------------------------------------------------------------------
 
 void free_workspace(helm_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
     for (auto& l : c->lv) {
         dfree(l.u0); dfree(l.u1); dfree(l.e); dfree(l.f); dfree(l.wf); dfree(l.we);
         l.u0 = l.u1 = l.e = l.f = l.wf = l.we = nullptr;
@@ -640,8 +652,10 @@ void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
     const long long vs = N * s;
     for (int pass = 0; pass < 2; ++pass) {
         c128* H = pass == 0 ? H1 : H2;
-        helm::launch_gram(c->L(), c->V, nb, vs, Wp, N, s, sb, c->partial, H, emulated(c));
-        helm::launch_combine<double>(c->L(), Wp, 1.0, -1.0, c->V, nb, vs, H, N, s, sb, emulated(c), c->csplit);
+        helm::launch_gram_f(c->L(), c->V, c->kfmt, nb, vs, Wp, c->kfmt, N, s, sb, c->partial, H,
+                            emulated(c));
+        helm::launch_combine_f(c->L(), Wp, c->kfmt, 1.0, -1.0, c->V, c->kfmt, nb, vs, H, N, s, sb,
+                               emulated(c), c->csplit);
     }
 }
 
@@ -649,8 +663,22 @@ void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
 // extra2: per column, the squared norm removed by that orthogonalisation
 // (sum of |H_ik|^2), so that extra2 + ||W_k||^2 is the column's squared norm
 // before it.  Win is left unchanged.
-helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
-                     const std::vector<double>& extra2, QRResult& out, bool& any_dep) {
+// First Gram of the block QR, enqueued with its copy to the host.  Split
+// from block_qr so that a caller can enqueue it before a synchronisation it
+// needs anyway.
+helm_status qr_gram_launch(helm_ctx* c, const c128* Win, int wfmt, int s, int sb) {
+    SmallLayout SL = small_layout(c, s, sb);
+    helm::launch_gram_f(c->L(), Win, wfmt, 1, 0, Win, wfmt, c->N(), s, sb, c->partial, c->small + SL.oG,
+                        emulated(c));
+    CUDA_TRY(c, cudaMemcpyAsync(c->hsmall + SL.oG, c->small + SL.oG, sizeof(c128) * SL.blk,
+                                cudaMemcpyDeviceToHost, c->st));
+    return HELM_OK;
+}
+
+// Win is in format wfmt; W2 and Vout are in the basis format c->kfmt.
+helm_status block_qr(helm_ctx* c, c128* Win, int wfmt, c128* Vout, int nb, int s, int sb,
+                     const std::vector<double>& extra2, QRResult& out, bool& any_dep,
+                     bool gram_enqueued = false) {
     const long long N = c->N();
     const int G = (s + sb - 1) / sb;
     SmallLayout SL = small_layout(c, s, sb);
@@ -663,9 +691,12 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
     std::vector<std::vector<cd>> R1(G), R2(G);
     std::vector<int> mask(s, 0);
     // pass 1
-    helm::launch_gram(c->L(), Win, 1, 0, Win, N, s, sb, c->partial, dG, emulated(c));
-    CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
-    helm_status st = sync(c);
+    helm_status st = HELM_OK;
+    if (!gram_enqueued) {
+        st = qr_gram_launch(c, Win, wfmt, s, sb);
+        if (st != HELM_OK) return st;
+    }
+    st = sync(c);
     if (st != HELM_OK) return st;
     for (int g = 0; g < G; ++g) {
         const int n = std::min(sb, s - g * sb);
@@ -687,19 +718,20 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
             if (dep[k]) { mask[g * sb + k] = 1; any_dep = true; }
     }
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
-    helm::launch_combine<double>(c->L(), c->W2, 0.0, 1.0, Win, 1, 0, dT, N, s, sb, emulated(c),
-                                 c->csplit);
+    helm::launch_combine_f(c->L(), c->W2, c->kfmt, 0.0, 1.0, Win, wfmt, 1, 0, dT, N, s, sb, emulated(c),
+                           c->csplit);
     if (any_dep) {
         CUDA_TRY(c, cudaMemcpyAsync(c->dmask, mask.data(), sizeof(int) * s, cudaMemcpyHostToDevice,
                                     c->st));
-        helm::launch_fill_random(c->L(), c->W2, N, s, c->dmask, c->rng_counter++);
+        helm::launch_fill_random_f(c->L(), c->W2, c->kfmt, N, s, c->dmask, c->rng_counter++);
         if (nb > 0) {
             c128* Hs = c->small + SL.oT;  // scratch; T already consumed
             cgs2(c, c->W2, nb, s, sb, Hs, Hs);
         }
     }
     // pass 2
-    helm::launch_gram(c->L(), c->W2, 1, 0, c->W2, N, s, sb, c->partial, dG, emulated(c));
+    helm::launch_gram_f(c->L(), c->W2, c->kfmt, 1, 0, c->W2, c->kfmt, N, s, sb, c->partial, dG,
+                        emulated(c));
     CUDA_TRY(c, cudaMemcpyAsync(hG, dG, sizeof(c128) * SL.blk, cudaMemcpyDeviceToHost, c->st));
     st = sync(c);
     if (st != HELM_OK) return st;
@@ -726,8 +758,8 @@ helm_status block_qr(helm_ctx* c, c128* Win, c128* Vout, int nb, int s, int sb,
         out.R[g] = Rg;
     }
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
-    helm::launch_combine<double>(c->L(), Vout, 0.0, 1.0, c->W2, 1, 0, dT, N, s, sb, emulated(c),
-                                 c->csplit);
+    helm::launch_combine_f(c->L(), Vout, c->kfmt, 0.0, 1.0, c->W2, c->kfmt, 1, 0, dT, N, s, sb,
+                           emulated(c), c->csplit);
     return HELM_OK;
 }
 
@@ -797,8 +829,96 @@ void learned_stage(helm_ctx* c, const c128* v, c64* z, int s) {
 // block FGMRES (Sec. 5.3)
 // ---------------------------------------------------------------------------
 
+// The device work of FGMRES step j, up to the first host synchronisation:
+// Z_j = cycle(V_j) [+ learned stage], W = A Z_j, two Gram-Schmidt passes
+// against V_0..V_j, the first Gram of the block QR of W, and the copies of
+// the Gram-Schmidt coefficients and that Gram to the host.
+template <typename ZT>
+helm_status fgmres_step_launches(helm_ctx* c, int j, int s, int sb) {
+    const long long vs = c->N() * s;
+    SmallLayout SL = small_layout(c, s, sb);
+    cplx<ZT>* Zj = reinterpret_cast<cplx<ZT>*>(c->Z) + (long long)j * vs;
+    bool done = false;
+    if constexpr (std::is_same<ZT, float>::value)
+        if (c->kfmt == helm::FMT_DD) {
+            // V_j as float pairs: the complex64 cycle takes its hi plane (the
+            // FP64 value truncated to FP32); W = A Z_j is written as pairs
+            cycle<float, float>(c, 0, reinterpret_cast<const c64*>(c->V + (long long)j * vs), Zj, s);
+            helm::launch_apply_dd(c->L(), fine_op<double>(c, false), Zj, reinterpret_cast<c64*>(c->W), s);
+            done = true;
+        }
+    if (!done) {
+        cycle<ZT, double>(c, 0, c->V + (long long)j * vs, Zj, s);
+        if constexpr (std::is_same<ZT, float>::value)
+            if (c->p.prec == HELM_MIXED_C64_LEARNED) learned_stage(c, c->V + (long long)j * vs, Zj, s);
+        helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), fine_op<double>(c, false), Zj,
+                                                                     c->W, s);
+    }
+    cgs2(c, c->W, j + 1, s, sb, c->small + SL.oH1, c->small + SL.oH2);
+    CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * 2 * SL.oH2, cudaMemcpyDeviceToHost,
+                                c->st));
+    return qr_gram_launch(c, c->W, c->kfmt, s, sb);
+}
+
+bool use_graphs(const helm_ctx* c, int s) {
+    if (c->prof || c->p.prec == HELM_MIXED_C64_LEARNED || c->p.graphs == 0) return false;
+    return c->p.graphs == 1 || c->N() * (long long)s <= (4LL << 20);
+}
+
+// fgmres_step_launches, replayed from a CUDA graph when use_graphs() says so.
+// The graph is captured on the context's private stream on first use of
+// (s, j) and launched on the context's stream; the launch counter advances
+// by the captured kernel count at each replay.
+template <typename ZT>
+helm_status fgmres_step(helm_ctx* c, int j, int s, int sb) {
+    if (!use_graphs(c, s)) return fgmres_step_launches<ZT>(c, j, s, sb);
+    for (auto& g : c->graphs)
+        if (g.s == s && g.j == j) {
+            CUDA_TRY(c, cudaGraphLaunch(g.exec, c->st));
+            c->launches += g.launches;
+            return HELM_OK;
+        }
+    if (!c->cap_st) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+    cudaStream_t user = c->st;
+    const long long before = c->launches;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeRelaxed));
+    c->st = c->cap_st;
+    helm_status st = fgmres_step_launches<ZT>(c, j, s, sb);
+    c->st = user;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_st, &graph);
+    const long long captured = c->launches - before;
+    c->launches = before;
+    if (st != HELM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(c, HELM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, HELM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    c->graphs.push_back({s, j, exec, captured});
+    CUDA_TRY(c, cudaGraphLaunch(exec, c->st));
+    c->launches += captured;
+    return HELM_OK;
+}
+
+template <typename ZT>
+helm_status fgmres_run(helm_ctx* c, int s, double tol, helm_info* info);
+
 template <typename ZT>
 helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
+    const int sb = std::min(c->p.block, s);
+    c->kfmt = (std::is_same<ZT, float>::value && c->p.prec == HELM_MIXED_C64 && helm::dd_formats_ok(s, sb))
+                  ? helm::FMT_DD : helm::FMT_C128;
+    helm_status st = fgmres_run<ZT>(c, s, tol, info);
+    c->kfmt = helm::FMT_C128;
+    return st;
+}
+
+template <typename ZT>
+helm_status fgmres_run(helm_ctx* c, int s, double tol, helm_info* info) {
     const long long N = c->N();
     const long long vs = N * s;
     const int m = c->p.restart;
@@ -851,7 +971,7 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
         // V_0 Lambda = R
         QRResult qr;
         bool dep;
-        st = block_qr(c, c->R, c->V, 0, s, sb, std::vector<double>(s, 0.0), qr, dep);
+        st = block_qr(c, c->R, helm::FMT_C128, c->V, 0, s, sb, std::vector<double>(s, 0.0), qr, dep);
         if (st != HELM_OK) return st;
         std::vector<BlockLS> ls(G);
         for (int g = 0; g < G; ++g) ls[g].init(sb, m, qr.R[g]);
@@ -860,16 +980,8 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
         int jend = m - 1;
         for (int j = 0; j < m; ++j) {
             // Z_j = M^{-1}_cycle V_j ; W = A Z_j
-            cplx<ZT>* Zj = Z + (long long)j * vs;
-            cycle<ZT, double>(c, 0, c->V + (long long)j * vs, Zj, s);
-            if constexpr (std::is_same<ZT, float>::value)
-                if (c->p.prec == HELM_MIXED_C64_LEARNED) learned_stage(c, c->V + (long long)j * vs, Zj, s);
-            helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), opA, Zj, c->W, s);
-            c128* H1 = c->small + SL.oH1;
-            c128* H2 = c->small + SL.oH2;
-            cgs2(c, c->W, j + 1, s, sb, H1, H2);
-            CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * 2 * SL.oH2,
-                                        cudaMemcpyDeviceToHost, c->st));
+            st = fgmres_step<ZT>(c, j, s, sb);
+            if (st != HELM_OK) return st;
             st = sync(c);
             if (st != HELM_OK) return st;
             // H_{i,j} = H1 + H2 per group, and the reference norms
@@ -890,7 +1002,8 @@ helm_status fgmres(helm_ctx* c, int s, double tol, helm_info* info) {
                         }
                 }
             // W = V_{j+1} H_{j+1,j}
-            st = block_qr(c, c->W, c->V + (long long)(j + 1) * vs, j + 1, s, sb, ref2, qr, dep);
+            st = block_qr(c, c->W, c->kfmt, c->V + (long long)(j + 1) * vs, j + 1, s, sb, ref2, qr, dep,
+                          true);
             if (st != HELM_OK) return st;
             bool all_stop = true;
             for (int g = 0; g < G; ++g) {
@@ -1193,6 +1306,7 @@ void helm_default_params(helm_params* p) {
     p->coarse_tf32x3 = 0;
     p->cycle_gamma = 1;
     p->krylov = 0;
+    p->graphs = 2;
 }
 
 helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_params* p,
@@ -1410,6 +1524,7 @@ void helm_destroy(helm_ctx* c) {
     delete c->prof;
     c->prof = nullptr;
     free_workspace(c);
+    if (c->cap_st) cudaStreamDestroy(c->cap_st);
     for (auto& l : c->lv) {
         dfree(l.coef); dfree(l.dinv); dfree(l.coef32); dfree(l.dinv32);
     }

@@ -42,7 +42,7 @@ class HelmParams(ctypes.Structure):
                 ("block", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("prec", ctypes.c_int), ("learned_weights", ctypes.c_void_p),
                 ("coarse_tf32x3", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
-                ("krylov", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -171,7 +171,8 @@ class Solver:
                  levels: int = 3, pre: int = 2, post: int = 2, jacobi_w: float = 0.8,
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
                  prec: str = "c128", stream=None, coarse_tf32x3: bool = False,
-                 learned_weights=None, cycle: str = "V", krylov: str = "fgmres"):
+                 learned_weights=None, cycle: str = "V", krylov: str = "fgmres",
+                 graphs: str = "auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libhelm needs a CUDA device")
@@ -199,6 +200,7 @@ class Solver:
         p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
         p.cycle_gamma = {"V": 1, "W": 2, "K": 3}[cycle]
         p.krylov = {"fgmres": 0, "bicgstab": 1}[krylov]
+        p.graphs = {"off": 0, "on": 1, "auto": 2}[graphs]
         self.learned_weights = learned_weights        # keeps the blob alive
         p.learned_weights = _ptr(learned_weights) if learned_weights is not None else None
         self.params = p

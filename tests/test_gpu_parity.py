@@ -299,6 +299,27 @@ def test_not_converged_returns_best_iterate(H):
     assert np.all(rr < 1.0)
 
 
+@pytest.mark.parametrize("prec,cycle", [("c128", "V"), ("c64", "V"), ("c64", "K")])
+def test_graph_replay_matches_direct_launches(H, prec, cycle):
+    """The FGMRES step replayed from CUDA graphs gives the directly launched
+    solve bit for bit, with the same cycle counts and kernel launch count
+    (two solves: the second replays the captured graphs)."""
+    P = I.random_problem_2d(55, (64, 32), 25.0, 5.0, 6, width=6, levels=3)
+    Q = dev(P.rhs())
+    out = {}
+    for mode in ("off", "on"):
+        S = H.Solver(P.m, P.gamma, P.h, P.omega, levels=3, block=3, restart=5, prec=prec,
+                     cycle=cycle, graphs=mode)
+        U1, i1, _ = S.solve(Q, tol=1e-8)
+        n0 = S.kernel_launches
+        U2, i2, _ = S.solve(Q, tol=1e-8)
+        out[mode] = (U1, U2, i1.iters.copy(), S.kernel_launches - n0)
+    assert torch.equal(out["off"][0], out["on"][0])
+    assert torch.equal(out["off"][1], out["on"][1])
+    np.testing.assert_array_equal(out["off"][2], out["on"][2])
+    assert out["off"][3] == out["on"][3] > 0
+
+
 def test_solve_batch_matches_single_solves(H):
     """helm_solve_batch over contexts of different grids, frequencies and
     precisions, each on its own stream, gives the single-solve results."""
