@@ -212,14 +212,29 @@ __global__ void k_build_aprime(const c128* __restrict__ Minv, int nc, float* __r
 
 int dense_tc_kpad(int nc) { return ((2 * nc + TBK - 1) / TBK) * TBK; }
 int dense_tc_ldb(int s) { return ((2 * s + TBN - 1) / TBN) * TBN; }
-int dense_tc_ksplit(int nc) {
-    int mt = (nc + TBM - 1) / TBM;
-    int ks = (2 * 152 + mt - 1) / mt;       // about two CTAs per SM
-    return ks < 1 ? 1 : (ks > 16 ? 16 : ks);
+constexpr int kMaxKSplit = 16;
+
+// K split for an nc x 2nc by 2nc x 2s product: the count of CTAs is
+// mt * nt * KS with two CTAs resident per SM (shared memory), so the time goes
+// as (waves) x (K tiles per CTA); each split adds a pass of the reduction over
+// nc x 2s floats (about 0.9 K-tile-waves at full bandwidth).  The KS in
+// 1..16 with the smallest such cost avoids a nearly empty last wave.
+int dense_tc_ksplit(int nc, int s) {
+    const int mt = (nc + TBM - 1) / TBM, nt = dense_tc_ldb(s) / TBN;
+    const int kt = dense_tc_kpad(nc) / TBK;
+    const long long slots = 2LL * 152;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int ks = 1; ks <= kMaxKSplit; ++ks) {
+        long long ctas = (long long)mt * nt * ks;
+        long long waves = (ctas + slots - 1) / slots;
+        double cost = (double)waves * ((kt + ks - 1) / ks) + 0.9 * ks * nt;
+        if (cost < best_cost) { best_cost = cost; best = ks; }
+    }
+    return best;
 }
 size_t dense_tc_scratch_floats(int nc, int s) {
-    return (size_t)dense_tc_kpad(nc) * dense_tc_ldb(s) +
-           (size_t)dense_tc_ksplit(nc) * nc * dense_tc_ldb(s);
+    return (size_t)dense_tc_kpad(nc) * dense_tc_ldb(s) + (size_t)kMaxKSplit * nc * dense_tc_ldb(s);
 }
 
 void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, bool split3) {
@@ -232,7 +247,7 @@ void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, b
 
 void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
                      float* scratch, bool split3) {
-    const int Kp = dense_tc_kpad(nc), ldb = dense_tc_ldb(s), KS = dense_tc_ksplit(nc);
+    const int Kp = dense_tc_kpad(nc), ldb = dense_tc_ldb(s), KS = dense_tc_ksplit(nc, s);
     float* Bp = scratch;
     float* P = scratch + (size_t)Kp * ldb;
     long long nb = (long long)Kp * ldb;

@@ -10,9 +10,13 @@ namespace helm {
 // y = Op x  (T: arithmetic precision; U: input element; V: output element)
 template <typename T, typename U, typename V, typename Op>
 void launch_apply(const Launch& L, const Op& op, const cplx<U>* x, cplx<V>* y, int s);
-// y = A x on the fine grid in FP64 arithmetic, x complex64, y written as an
-// FMT_DD block (two complex64 planes of N*s, hi then lo; needs s <= 512)
-void launch_apply_dd(const Launch& L, const FineOp<double>& op, const c64* x, c64* y, int s);
+// y = A x on the fine grid, x complex64, in double-float arithmetic (1/h^2
+// and the mass coefficients cdd as float pairs), y written as an FMT_DD block
+// (two complex64 planes of N*s, hi then lo); needs s <= 512
+void launch_apply_dd(const Launch& L, const Grid& g, double inv_h2, const float4* cdd, const c64* x,
+                     c64* y, int s);
+// complex128 values -> float pairs (re hi, re lo, im hi, im lo)
+void launch_split_pairs(const Launch& L, const c128* in, float4* out, long long n);
 
 // r = b - Op x
 template <typename T, typename Op>
@@ -56,7 +60,7 @@ void launch_dense_apply(const Launch& L, const cplx<T>* Minv, int n, const cplx<
 // and the scratch (floats) one launch needs for nc coarse nodes and s columns
 int dense_tc_kpad(int nc);
 int dense_tc_ldb(int s);
-int dense_tc_ksplit(int nc);
+int dense_tc_ksplit(int nc, int s);
 size_t dense_tc_scratch_floats(int nc, int s);
 // A' (nc x dense_tc_kpad(nc) floats): interleaved (re, im) of Minv in FP32,
 // rounded to tf32 unless split3 (the three-product solve splits it itself)

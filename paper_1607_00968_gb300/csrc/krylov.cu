@@ -93,24 +93,35 @@ __global__ void __launch_bounds__(kThreads) k_gram(const c128* __restrict__ X, l
     }
 }
 
-// out[e] = sum over chunks of partial[c][e]: 32 entries per CTA, the 8 warps
-// of the CTA take every 8th chunk and are summed in shared memory.
-__global__ void __launch_bounds__(256) k_gram_reduce(const c128* __restrict__ partial, int chunks,
-                                                     long long E, c128* __restrict__ out) {
-    __shared__ double2 red[8][32];
+// out[e] = sum over chunks of partial[c][e]: 32 entries per CTA, the 32 warps
+// of the CTA take every 32nd chunk and are summed in shared memory (fixed
+// order: the result does not depend on timing).
+constexpr int kReduceWarps = 32;
+__global__ void __launch_bounds__(32 * kReduceWarps) k_gram_reduce(const c128* __restrict__ partial,
+                                                                   int chunks, long long E,
+                                                                   c128* __restrict__ out) {
+    __shared__ double2 red[kReduceWarps][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long e = (long long)blockIdx.x * 32 + lane;
     double re = 0.0, im = 0.0;
     if (e < E)
-        for (int c = w; c < chunks; c += 8) {
-            c128 v = partial[(long long)c * E + e];
-            re += v.re;
-            im += v.im;
+        for (int c = w; c < chunks; c += 4 * kReduceWarps) {
+            c128 v[4];     // four independent loads in flight per thread
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int cu = c + u * kReduceWarps;
+                v[u] = cu < chunks ? partial[(long long)cu * E + e] : mk(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                re += v[u].re;
+                im += v[u].im;
+            }
         }
     red[w][lane] = make_double2(re, im);
     __syncthreads();
     if (w == 0 && e < E) {
-        for (int k = 1; k < 8; ++k) { re += red[k][lane].x; im += red[k][lane].y; }
+        for (int k = 1; k < kReduceWarps; ++k) { re += red[k][lane].x; im += red[k][lane].y; }
         out[e] = mk(re, im);
     }
 }
@@ -617,7 +628,7 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
     L.post();
     long long E = E1 * nb;
     L.pre(KID_GRAM_REDUCE, (chunks + 1.0) * E * 16.0, 2.0 * chunks * E);
-    k_gram_reduce<<<(unsigned)((E + 31) / 32), 256, 0, L.st>>>(partial, chunks, E, out);
+    k_gram_reduce<<<(unsigned)((E + 31) / 32), 32 * kReduceWarps, 0, L.st>>>(partial, chunks, E, out);
     L.post();
 }
 
@@ -717,6 +728,12 @@ void launch_from_internal(const Launch& L, const c128* internal, c128* abi, long
     dim3 grid((unsigned)((N + 31) / 32), (s + 31) / 32);
     L.pre(KID_LAYOUT, 32.0 * N * s, 0);
     k_from_internal<<<grid, dim3(32, 8), 0, L.st>>>(internal, abi, N, s, conjugate ? 1 : 0);
+    L.post();
+}
+
+void launch_split_pairs(const Launch& L, const c128* in, float4* out, long long n) {
+    L.pre(KID_LAYOUT, 32.0 * n, 0);
+    k_split<<<blocks_for(n), kThreads, 0, L.st>>>(in, out, n);
     L.post();
 }
 

@@ -190,22 +190,96 @@ __global__ void __launch_bounds__(256) k_apply_v(Op op, const cplx<U>* __restric
     stR<V, R>(yout + e0, w);
 }
 
-// FP64 apply with the result split into an unevaluated float pair per
-// component (hi plane at y, lo plane at y + N*s)
+// error-free a + b = s + e (TwoSum)
+__device__ __forceinline__ void ddf_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// (S, E) += t for a float t (E gathers the rounding errors)
+__device__ __forceinline__ void ddf_add(float& S, float& E, float t) {
+    float e;
+    ddf_two_sum(S, t, S, e);
+    E = __fadd_rn(E, e);
+}
+
+// (S, E) -= (ch + cl) u: the product's high part exactly by FMA, the cross
+// term c_lo u into the error
+__device__ __forceinline__ void ddf_sub_prod(float& S, float& E, float ch, float cl, float u) {
+    float q = __fmul_rn(ch, u);
+    float qe = __fmaf_rn(ch, u, -q);
+    qe = __fmaf_rn(cl, u, qe);
+    float e;
+    ddf_two_sum(S, -q, S, e);
+    E = __fadd_rn(E, __fsub_rn(e, qe));
+}
+
+// y = A x on the fine grid for complex64 x, in double-float arithmetic on
+// the FP32 pipes: the 2d u_i - sum of neighbours is summed error-free, scaled
+// by 1/h^2 = ih + il and reduced by c_i u_i with c_i = (re hi, re lo, im hi,
+// im lo); each component ends as a renormalised pair, written to the hi plane
+// (y) and the lo plane (y + N*s).  About 2^-46 relative to the largest term.
 template <int R>
-__global__ void __launch_bounds__(256) k_apply_dd(FineOp<double> op, const c64* __restrict__ xin,
-                                                   c64* __restrict__ yout, int s) {
-    VGEO_PROLOGUE(op.g)
-    c128 o[R];
-    op.template applyR<R>(xin, node, x, y, z, s, r0, o);
+__global__ void __launch_bounds__(256) k_apply_dd(Grid g, float ih, float il, const float4* __restrict__ cdd,
+                                                   const c64* __restrict__ xin, c64* __restrict__ yout,
+                                                   int s) {
+    VGEO_PROLOGUE(g)
+    const c64* p = xin + e0;
+    const CV<float, R> ui = ldR<float, R>(p);
+    float S[R][2], E[R][2];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        S[k][0] = 4.f * ui.v[k].re;            // exact
+        S[k][1] = 4.f * ui.v[k].im;
+        E[k][0] = E[k][1] = 0.f;
+        if (g.dim == 3) {
+            ddf_add(S[k][0], E[k][0], 2.f * ui.v[k].re);
+            ddf_add(S[k][1], E[k][1], 2.f * ui.v[k].im);
+        }
+    }
+    auto sub = [&](const c64* q) {
+        CV<float, R> v = ldR<float, R>(q);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            ddf_add(S[k][0], E[k][0], -v.v[k].re);
+            ddf_add(S[k][1], E[k][1], -v.v[k].im);
+        }
+    };
+    if (x > 0) sub(p - s);
+    if (x < g.n1 - 1) sub(p + s);
+    const long long sy = (long long)g.n1 * s;
+    if (y > 0) sub(p - sy);
+    if (y < g.n2 - 1) sub(p + sy);
+    if (g.dim == 3) {
+        const long long sz = (long long)g.n1 * g.n2 * s;
+        if (z > 0) sub(p - sz);
+        if (z < g.n3 - 1) sub(p + sz);
+    }
+    const float4 c = __ldg(cdd + node);
     CV<float, R> hi, lo;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-        split_d(o[k].re, hi.v[k].re, lo.v[k].re);
-        split_d(o[k].im, hi.v[k].im, lo.v[k].im);
+        float T[2], Te[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            // (S + E) (ih + il)
+            T[q] = __fmul_rn(S[k][q], ih);
+            Te[q] = __fmaf_rn(S[k][q], ih, -T[q]);
+            Te[q] = __fmaf_rn(S[k][q], il, Te[q]);
+            Te[q] = __fmaf_rn(E[k][q], ih, Te[q]);
+        }
+        // - c u:  re -= cr ur - ci ui ;  im -= cr ui + ci ur
+        ddf_sub_prod(T[0], Te[0], c.x, c.y, ui.v[k].re);
+        ddf_sub_prod(T[0], Te[0], -c.z, -c.w, ui.v[k].im);
+        ddf_sub_prod(T[1], Te[1], c.x, c.y, ui.v[k].im);
+        ddf_sub_prod(T[1], Te[1], c.z, c.w, ui.v[k].re);
+        ddf_two_sum(T[0], Te[0], hi.v[k].re, lo.v[k].re);
+        ddf_two_sum(T[1], Te[1], hi.v[k].im, lo.v[k].im);
     }
     stR<float, R>(yout + e0, hi);
-    stR<float, R>(yout + op.g.N * s + e0, lo);
+    stR<float, R>(yout + g.N * s + e0, lo);
 }
 
 template <typename T, typename FT, typename Op, int R>
@@ -608,13 +682,15 @@ template <typename T> struct OpCost<GalOp<T>> {
     static constexpr bool fine = false;
 };
 
-void launch_apply_dd(const Launch& L, const FineOp<double>& op, const c64* x, c64* y, int s) {
-    long long total = op.g.N * s;
-    L.pre(KID_APPLY_FINE, total * (8.0 + 16.0) + op.g.N * OpCost<FineOp<double>>::coef_bytes(op),
-          total * OpCost<FineOp<double>>::flops(op));
-    Geo G = geo_for(op.g, s);
-    if (G.R == 2) k_apply_dd<2><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
-    else k_apply_dd<1><<<G.grid, G.block, 0, L.st>>>(op, x, y, s);
+void launch_apply_dd(const Launch& L, const Grid& g, double inv_h2, const float4* cdd, const c64* x,
+                     c64* y, int s) {
+    long long total = g.N * s;
+    L.pre(KID_APPLY_FINE, total * (8.0 + 16.0) + g.N * 16.0, total * (g.dim == 3 ? 22.0 : 18.0));
+    const float ih = (float)inv_h2;
+    const float il = (float)(inv_h2 - (double)ih);
+    Geo G = geo_for(g, s);
+    if (G.R == 2) k_apply_dd<2><<<G.grid, G.block, 0, L.st>>>(g, ih, il, cdd, x, y, s);
+    else k_apply_dd<1><<<G.grid, G.block, 0, L.st>>>(g, ih, il, cdd, x, y, s);
     L.post();
 }
 

@@ -133,6 +133,7 @@ struct helm_ctx {
     c128* cA = nullptr;
     c128* cM = nullptr;
     c64* cA32 = nullptr;
+    float4* cAdd = nullptr;   // c_A as float pairs (double-float A Z)
     c64* cM32 = nullptr;
     // coarsest inverse
     int nc = 0;
@@ -844,7 +845,7 @@ helm_status fgmres_step_launches(helm_ctx* c, int j, int s, int sb) {
             // V_j as float pairs: the complex64 cycle takes its hi plane (the
             // FP64 value truncated to FP32); W = A Z_j is written as pairs
             cycle<float, float>(c, 0, reinterpret_cast<const c64*>(c->V + (long long)j * vs), Zj, s);
-            helm::launch_apply_dd(c->L(), fine_op<double>(c, false), Zj, reinterpret_cast<c64*>(c->W), s);
+            helm::launch_apply_dd(c->L(), c->lv[0].g, c->inv_h2, c->cAdd, Zj, reinterpret_cast<c64*>(c->W), s);
             done = true;
         }
     if (!done) {
@@ -1394,6 +1395,8 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
     SETUP_TRY(dalloc(&c->kappa, sizeof(float) * N0));
     helm::launch_kappa(L, c->cA, N0, p->h * p->h, c->kappa);
     helm::launch_round_c64(L, c->cA, c->cA32, N0);
+    SETUP_TRY(dalloc(&c->cAdd, sizeof(float4) * N0));
+    helm::launch_split_pairs(L, c->cA, c->cAdd, N0);
     helm::launch_round_c64(L, c->cM, c->cM32, N0);
     for (int l = 0; l < p->levels; ++l) {
         long long Nl = c->lv[l].g.N;
@@ -1529,6 +1532,7 @@ void helm_destroy(helm_ctx* c) {
         dfree(l.coef); dfree(l.dinv); dfree(l.coef32); dfree(l.dinv32);
     }
     dfree(c->cA); dfree(c->cM); dfree(c->cA32); dfree(c->cM32); dfree(c->Minv); dfree(c->Minv32);
+    dfree(c->cAdd);
     dfree(c->Ap);
     dfree(c->kappa);
     dfree(c->dadm);
