@@ -38,6 +38,11 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, 152 SMs x ~2 FMA/clk x 2070 MHz
 # double-float peak in FP64-equivalent flops: 152 SMs x 128 FP32 lanes x 2.07 GHz
 # = 40.3 T instructions/s; one complex double-float MAC = 48 instructions = 8 flops
 DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
+# Measured DRAM bytes (read + write, ncu) over algorithmic bytes for a kernel
+# class, from six launches of one 5 Hz salt solve: reads match the
+# algorithmic count, about 40% of the written bytes are still in L2 when the
+# launch ends.  Valid while the kernel is unchanged.
+TRAFFIC_RATIO = {"combine_dd": (0.847, "profiles/traffic_salt2d_512x256_5hz.md")}
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
 SOLVER = dict(pre=2, post=2, jacobi_w=0.8)
@@ -396,13 +401,32 @@ def main():
     for _ in range(args.warmup):
         for S in mixed:
             S.solve(Qd, TOL)
+
+    def merged_profile():
+        out = {}
+        for S in mixed:
+            for k, v in S.profile_read().items():
+                p = out.setdefault(k, dict(time_ms=0.0, launches=0, bytes=0.0, flops=0.0))
+                for kk in p:
+                    p[kk] += v[kk]
+        return out
+
+    # one more (untimed) step with every kernel class profiled: the kernel
+    # table and the dominant class; the timed steps then record that class only
     for S in mixed:
         S.profile(True)
+        S.solve(Qd, TOL)
+    prof = merged_profile()
+    dom = max(prof, key=lambda k: prof[k]["time_ms"])
+    for S in mixed:
+        S.profile(True, only=dom)
     launches0 = sum(S.kernel_launches for S in mixed)
     clk = ClockSampler(local)
     clk.start()
     barrier()
+    torch.cuda.profiler.start()             # bounds an external profiler's capture
     ms, infos = timed_steps(torch, mixed, Qd, args.steps, stream)
+    torch.cuda.profiler.stop()
     barrier()
     clocks = clk.stop()
     launches = sum(S.kernel_launches for S in mixed) - launches0
@@ -411,25 +435,19 @@ def main():
     iters = [int(np.max(i.iters)) for i in infos]
     relres = float(max(np.max(i.relres) for i in infos))
 
-    # per-kernel roofline from the profiler (events over the timed region)
-    prof = {}
+    # roofline of the dominant class from its events over the timed region
+    d = merged_profile()[dom]
     for S in mixed:
-        for k, v in S.profile_read().items():
-            p = prof.setdefault(k, dict(time_ms=0.0, launches=0, bytes=0.0, flops=0.0))
-            for kk in p:
-                p[kk] += v[kk]
         S.profile(False)
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     kernels = {}
-    for k, v in prof.items():
+    for k, v in prof.items():                  # the profiled untimed step
         if v["launches"] == 0 or v["time_ms"] <= 0:
             continue
         gbs = v["bytes"] / (v["time_ms"] / 1e3) / 1e9
         tfl = v["flops"] / (v["time_ms"] / 1e3) / 1e12
-        kernels[k] = {"ms_per_step": v["time_ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+        kernels[k] = {"ms_per_step": v["time_ms"], "launches_per_step": v["launches"],
                       "GB/s": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4), "TFLOP/s": round(tfl, 3)}
-    dom = max(prof, key=lambda k: prof[k]["time_ms"])
-    d = prof[dom]
     fp64_kernels = ("gram", "combine", "residual_fp64", "gram_reduce", "apply_fine")
     dd_kernels = ("gram_dd", "combine_dd")
     if dom in fp64_kernels or dom in dd_kernels:
@@ -446,6 +464,13 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
                 "peak_source": "hbm_gbs of %s" % peak_src}
     roof["share_of_step"] = round(d["time_ms"] / ms, 4) if ms > 0 else None
+    roof["launches"] = d["launches"]
+    if dom in TRAFFIC_RATIO and d["launches"]:
+        # DRAM bytes per launch: the algorithmic bytes of the average timed
+        # launch times the measured DRAM/algorithmic ratio of this kernel
+        roof["traffic"] = round(TRAFFIC_RATIO[dom][0] * d["bytes"] / d["launches"])
+        roof["traffic_unit"] = "bytes per launch"
+        roof["traffic_source"] = TRAFFIC_RATIO[dom][1]
 
     # ---------------- end to end through the host-buffer entry ----------------
     Qh = torch.as_tensor(Q).pin_memory()

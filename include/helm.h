@@ -354,6 +354,11 @@ helm_status helm_fwi_gradient(helm_ctx* ctx, const void* Q, int s, const void* d
  * once per node).  Enabling resets the totals; disabling frees the events.
  * ------------------------------------------------------------------- */
 helm_status helm_profile_enable(helm_ctx* ctx, int enable);
+/* While the profiler is enabled, record only launches of class kid (their
+   event pairs, bytes and flops); -1 records every class (the state after
+   helm_profile_enable).  HELM_ERR_ARG if the profiler is off or kid is out
+   of range.  Fewer events in flight perturb the timed work less. */
+helm_status helm_profile_select(helm_ctx* ctx, int kid);
 /* Number of kernel classes and the name of class kid (static strings). */
 int helm_profile_kernel_count(void);
 const char* helm_profile_kernel_name(int kid);

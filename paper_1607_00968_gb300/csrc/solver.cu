@@ -74,6 +74,8 @@ struct Profiler {
     double bytes[KID_COUNT] = {};
     double flops[KID_COUNT] = {};
     long long launches[KID_COUNT] = {};
+    int only = -1;       // record one kernel class only (-1: all)
+    bool armed = false;  // the current launch is being recorded
 
     cudaEvent_t get() {
         if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
@@ -106,6 +108,8 @@ struct Profiler {
 };
 
 void prof_begin(Profiler* p, cudaStream_t st, int kid, double bytes, double flops) {
+    p->armed = p->only < 0 || kid == p->only;
+    if (!p->armed) return;
     Profiler::Rec r{kid, bytes, flops, p->get(), p->get()};
     cudaEventRecord(r.a, st);
     p->open.push_back(r);
@@ -116,7 +120,8 @@ void prof_begin(Profiler* p, cudaStream_t st, int kid, double bytes, double flop
 }
 
 void prof_end(Profiler* p, cudaStream_t st) {
-    if (p->open.empty()) return;
+    if (!p->armed || p->open.empty()) return;
+    p->armed = false;
     cudaEventRecord(p->open.back().b, st);
     if (p->open.size() > 4096) p->resolve();
 }
@@ -1759,6 +1764,14 @@ helm_status helm_profile_enable(helm_ctx* c, int enable) {
         delete c->prof;
         c->prof = nullptr;
     }
+    return HELM_OK;
+}
+
+helm_status helm_profile_select(helm_ctx* c, int kid) {
+    if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
+    if (kid < -1 || kid >= helm::KID_COUNT) return fail(c, HELM_ERR_ARG, "kernel class out of range");
+    if (!c->prof) return fail(c, HELM_ERR_ARG, "the profiler is not enabled");
+    c->prof->only = kid;
     return HELM_OK;
 }
 

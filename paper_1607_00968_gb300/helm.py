@@ -26,7 +26,8 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_solve_batch", "helm_destroy", "helm_last_error", "helm_level_shape",
            "helm_apply", "helm_smooth", "helm_restrict_residual", "helm_prolong_add",
            "helm_coarse_solve", "helm_vcycle", "helm_get_operator", "helm_kernel_launches",
-           "helm_profile_enable", "helm_profile_kernel_count", "helm_profile_kernel_name",
+           "helm_profile_enable", "helm_profile_select", "helm_profile_kernel_count",
+           "helm_profile_kernel_name",
            "helm_profile_read", "helm_vcycle_noalloc", "helm_learned_layers",
            "helm_learned_blob_bytes", "helm_learned_layer", "helm_conv3x3", "helm_conv3x3_wgrad",
            "helm_conv3x3_flip", "helm_adam", "helm_learned_input", "helm_learned_target",
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_get_operator": (i, [vp, i, vp]),
         "helm_kernel_launches": (ll, [vp]),
         "helm_profile_enable": (i, [vp, i]),
+        "helm_profile_select": (i, [vp, i]),
         "helm_profile_kernel_count": (i, []),
         "helm_profile_kernel_name": (ctypes.c_char_p, [i]),
         "helm_profile_read": (i, [vp, i, P(d), P(ll), P(d), P(d)]),
@@ -318,8 +320,14 @@ class Solver:
         return out
 
     # -- profiler ----------------------------------------------------------
-    def profile(self, enable: bool = True):
+    def profile(self, enable: bool = True, only: str | None = None):
+        """Enable (and reset) or disable the per-kernel profiler; `only`
+        restricts the recording to one kernel class (a profile_read name)."""
         self._check(self.lib.helm_profile_enable(self.ctx, 1 if enable else 0))
+        if enable and only is not None:
+            names = [self.lib.helm_profile_kernel_name(k).decode()
+                     for k in range(self.lib.helm_profile_kernel_count())]
+            self._check(self.lib.helm_profile_select(self.ctx, names.index(only)))
 
     def profile_read(self) -> dict:
         """{kernel name: dict(time_ms, launches, bytes, flops)} since enabling."""
