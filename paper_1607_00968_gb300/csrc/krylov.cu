@@ -362,6 +362,201 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X
     }
 }
 
+// ---------------------------------------------------------------------------
+// Groups of four columns (sb = 4, s a multiple of 4): a thread owns one group
+// and works straight from global memory, with no shared-memory staging.
+// ld4 reads the four columns g*4 .. g*4+3 of node row e0 (= node * s + g * 4)
+// as split float pairs, with 16-byte vector loads.
+// ---------------------------------------------------------------------------
+template <int F>
+__device__ __forceinline__ void ld4(const char* b, long long plane, long long e0, float4 (&v)[4]) {
+    if constexpr (F == FMT_DD) {
+        const float4* h = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + e0);
+        const float4* l = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + plane + e0);
+        float4 h0 = h[0], h1 = h[1], l0 = l[0], l1 = l[1];
+        v[0] = make_float4(h0.x, l0.x, h0.y, l0.y);
+        v[1] = make_float4(h0.z, l0.z, h0.w, l0.w);
+        v[2] = make_float4(h1.x, l1.x, h1.y, l1.y);
+        v[3] = make_float4(h1.z, l1.z, h1.w, l1.w);
+    } else if constexpr (F == FMT_C64) {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const c64*>(b) + e0);
+        float4 a0 = p[0], a1 = p[1];
+        v[0] = make_float4(a0.x, 0.f, a0.y, 0.f);
+        v[1] = make_float4(a0.z, 0.f, a0.w, 0.f);
+        v[2] = make_float4(a1.x, 0.f, a1.y, 0.f);
+        v[3] = make_float4(a1.z, 0.f, a1.w, 0.f);
+    } else {
+        const c128* p = reinterpret_cast<const c128*>(b) + e0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = split_c(p[a]);
+    }
+}
+
+// Gram of groups of four: thread (g, r) accumulates the 4 x 4 block
+// conj(X_i[node][g*4+a]) Y[node][g*4+b] over the nodes n0 + r, n0 + r + R, ...
+// of its CTA's chunk (R = 128 / G replicas), loading the next node while it
+// works on the current one; replicas are added in FP64 in shared memory and
+// each CTA writes one partial slot (layout of k_gram).
+template <int XF, int YF>
+__global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, long long xstride,
+                                                   const char* __restrict__ Y, long long N, int s,
+                                                   int chunks, c128* __restrict__ partial) {
+    extern __shared__ double2 red4[];              // R x G x 16
+    const int G = s / 4;
+    const int R = 128 / G;
+    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    const bool active = r < R;
+    const int i = blockIdx.y;
+    const char* Xi = X + (long long)i * xstride;
+    const long long plane = N * s;
+    const long long per = (N + chunks - 1) / chunks;
+    const long long n0 = (long long)blockIdx.x * per;
+    const long long n1 = n0 + per < N ? n0 + per : N;
+    float S[4][4][2], Lc[4][4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) S[a][b][0] = S[a][b][1] = Lc[a][b][0] = Lc[a][b][1] = 0.f;
+    float4 xc[4], yc[4], xn[4], yn[4];
+    long long n = n0 + r;
+    if (active && n < n1) {
+        ld4<XF>(Xi, plane, n * s + g * 4, xc);
+        ld4<YF>(Y, plane, n * s + g * 4, yc);
+    }
+    for (; active && n < n1; n += R) {
+        const long long nn = n + R;
+        if (nn < n1) {
+            ld4<XF>(Xi, plane, nn * s + g * 4, xn);
+            ld4<YF>(Y, plane, nn * s + g * 4, yn);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float4 x = xc[a], y = yc[b];
+                // conj(x) * y: re = xr yr + xi yi, im = xr yi - xi yr
+                dd_mac(S[a][b][0], Lc[a][b][0], x.x, x.y, y.x, y.y);
+                dd_mac(S[a][b][0], Lc[a][b][0], x.z, x.w, y.z, y.w);
+                dd_mac(S[a][b][1], Lc[a][b][1], x.x, x.y, y.z, y.w);
+                dd_mac(S[a][b][1], Lc[a][b][1], -x.z, -x.w, y.x, y.y);
+            }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { xc[a] = xn[a]; yc[a] = yn[a]; }
+    }
+    const int E1 = G * 16;
+    if (active)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                red4[(long long)(r * G + g) * 16 + a * 4 + b] =
+                    make_double2(f2d_bits(S[a][b][0]) + f2d_bits(Lc[a][b][0]),
+                                 f2d_bits(S[a][b][1]) + f2d_bits(Lc[a][b][1]));
+    __syncthreads();
+    c128* out = partial + ((long long)blockIdx.x * gridDim.y + i) * E1;
+    for (int e = threadIdx.x; e < E1; e += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < R; ++q) { re += red4[(long long)q * E1 + e].x; im += red4[(long long)q * E1 + e].y; }
+        out[e] = mk(re, im);
+    }
+}
+
+// Block update for groups of four: thread (node, g) forms the four outputs
+// of its group, sum_i sum_a X_i[node][g*4+a] C[i][g][a][b], from X_i read
+// straight from global memory (the next block's values loaded ahead) and the
+// split coefficients staged once per CTA in shared memory as [i][a][b][g]
+// (consecutive g in consecutive words: no bank conflicts).
+template <int XF, int OF>
+__global__ void __launch_bounds__(256) k_combine_sb4(char* __restrict__ out, double beta, double sign,
+                                                      const char* __restrict__ X, int nb,
+                                                      long long xstride,
+                                                      const float4* __restrict__ Cs, long long N,
+                                                      int s) {
+    extern __shared__ float4 cs4[];                // nb x 4 x 4 x G
+    const int G = s / 4;
+    const int nc = nb * G * 16;
+    for (int idx = threadIdx.x; idx < nc; idx += blockDim.x) {
+        // source [i][g][a][b] -> [i][a][b][g]
+        int i = idx / (G * 16), rem = idx - i * G * 16;
+        int g = rem / 16, ab = rem - g * 16;
+        cs4[(i * 16 + ab) * G + g] = Cs[idx];
+    }
+    __syncthreads();
+    const long long plane = N * s;
+    const long long total = N * G;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long node = t / G;
+        const int g = (int)(t - node * G);
+        const long long e0 = node * s + g * 4;
+        float S[4][2], Lc[4][2];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) S[b][0] = S[b][1] = Lc[b][0] = Lc[b][1] = 0.f;
+        float4 xc[4], xn[4];
+        ld4<XF>(X, plane, e0, xc);
+        for (int i = 0; i < nb; ++i) {
+            if (i + 1 < nb) ld4<XF>(X + (long long)(i + 1) * xstride, plane, e0, xn);
+            const float4* ci = cs4 + (long long)i * 16 * G + g;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float4 x = xc[a];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float4 c = ci[(a * 4 + b) * G];
+                    // x * c: re = xr cr - xi ci, im = xr ci + xi cr
+                    dd_mac(S[b][0], Lc[b][0], x.x, x.y, c.x, c.y);
+                    dd_mac(S[b][0], Lc[b][0], -x.z, -x.w, c.z, c.w);
+                    dd_mac(S[b][1], Lc[b][1], x.x, x.y, c.z, c.w);
+                    dd_mac(S[b][1], Lc[b][1], x.z, x.w, c.x, c.y);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xc[a] = xn[a];
+        }
+        if constexpr (OF == FMT_DD) {
+            float2* o = reinterpret_cast<float2*>(out);
+            float4 oh[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+            float4 ol[2] = {oh[0], oh[1]};
+            if (beta != 0.0) {
+                oh[0] = reinterpret_cast<const float4*>(o + e0)[0];
+                oh[1] = reinterpret_cast<const float4*>(o + e0)[1];
+                ol[0] = reinterpret_cast<const float4*>(o + plane + e0)[0];
+                ol[1] = reinterpret_cast<const float4*>(o + plane + e0)[1];
+            }
+            const float ohv[8] = {oh[0].x, oh[0].y, oh[0].z, oh[0].w, oh[1].x, oh[1].y, oh[1].z, oh[1].w};
+            const float olv[8] = {ol[0].x, ol[0].y, ol[0].z, ol[0].w, ol[1].x, ol[1].y, ol[1].z, ol[1].w};
+            float hv[8], lv[8];
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float sS = sign < 0.0 ? -S[b][q] : S[b][q];
+                    float sL = sign < 0.0 ? -Lc[b][q] : Lc[b][q];
+                    float t, err;
+                    two_sum(ohv[2 * b + q], sS, t, err);
+                    err = __fadd_rn(err, __fadd_rn(olv[2 * b + q], sL));
+                    two_sum(t, err, hv[2 * b + q], lv[2 * b + q]);
+                }
+            reinterpret_cast<float4*>(o + e0)[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            reinterpret_cast<float4*>(o + e0)[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+            reinterpret_cast<float4*>(o + plane + e0)[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+            reinterpret_cast<float4*>(o + plane + e0)[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+        } else {
+            c128* o = reinterpret_cast<c128*>(out) + e0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                double are = f2d_bits(S[b][0]) + f2d_bits(Lc[b][0]);
+                double aim = f2d_bits(S[b][1]) + f2d_bits(Lc[b][1]);
+                if (sign == -1.0) { are = -are; aim = -aim; }
+                else if (sign != 1.0) { are *= sign; aim *= sign; }
+                if (beta == 1.0) { c128 v = o[b]; are += v.re; aim += v.im; }
+                else if (beta != 0.0) { c128 v = o[b]; are += beta * v.re; aim += beta * v.im; }
+                o[b] = mk(are, aim);
+            }
+        }
+    }
+}
+
 constexpr int kCombineRows = 4;   // nodes per thread in the dd combine
 
 __global__ void k_split(const c128* __restrict__ C, float4* __restrict__ Cs, long long n) {
@@ -566,6 +761,14 @@ long long gram_partial_elems(long long N, int nb, int s, int sb) {
     return (long long)gram_chunks(N, nb, s) * nb * E1;
 }
 
+// CTAs of `kern` resident per SM at this launch shape (at least 1)
+template <typename K>
+int resident_ctas(K kern, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess) n = 1;
+    return n < 1 ? 1 : n;
+}
+
 bool gram_dd_ok(int s, int sb) {
     const int G = (s + sb - 1) / sb;
     const long long Q = (long long)G * sb * ((sb + 3) / 4);
@@ -604,7 +807,30 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
     dim3 grid(chunks, nb);
     const bool dd = emulate && gram_dd_ok(s, sb);
     L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
-    if (dd) {
+    if (dd && sb == 4 && s % 4 == 0 && s <= 512) {
+        // groups of four: 128-thread CTAs, about three per SM in one wave
+        const int G4 = s / 4;
+        const int R4 = 128 / G4;
+        const long long xsb = xstride * fmt_bytes(xf);
+        const size_t sm4 = (size_t)R4 * G4 * 16 * sizeof(double2);
+        const char* Xb = static_cast<const char*>(X);
+        const char* Yb = static_cast<const char*>(Y);
+        auto go = [&](auto kern) {
+            if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+            // one wave of resident CTAs over the nb blocks
+            long long tiles = (N + R4 - 1) / R4;
+            long long want = ((long long)resident_ctas(kern, 128, sm4) * 152 + nb - 1) / nb;
+            int ch = (int)(tiles < want ? tiles : want);
+            if (ch > chunks) ch = chunks;          // the partial buffer holds gram_chunks() slots
+            if (ch < 1) ch = 1;
+            kern<<<dim3(ch, nb), 128, sm4, L.st>>>(Xb, xsb, Yb, N, s, ch, partial);
+            chunks = ch;
+        };
+        if (xf == FMT_DD && yf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_DD>);
+        else if (xf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_C128>);
+        else if (yf == FMT_DD) go(k_gram_sb4<FMT_C128, FMT_DD>);
+        else go(k_gram_sb4<FMT_C128, FMT_C128>);
+    } else if (dd) {
         const int nbq = (sb + 3) / 4;
         const long long Q = (long long)G * sb * nbq;
         int qpt = (int)((Q + kThreads - 1) / kThreads);
@@ -667,6 +893,30 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
         L.pre(KID_COMBINE_DD, (double)N * s * (nb * xb + (beta != 0.0 ? 32.0 : 16.0)),
               8.0 * nb * (double)N * s * sb);
         const long long xsb = xstride * fmt_bytes(xf);
+        const size_t sm4 = (size_t)nb * G * 16 * sizeof(float4);
+        if (sb == 4 && s % 4 == 0 && sm4 <= 160 * 1024) {
+            const long long total = N * (s / 4);
+            auto go = [&](auto kern) {
+                if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+                // one wave of resident CTAs, grid-stride over (node, group)
+                long long want = (total + 255) / 256;
+                long long cap = (long long)resident_ctas(kern, 256, sm4) * 152;
+                const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+                kern<<<g4, 256, sm4, L.st>>>(static_cast<char*>(out), beta, sign, static_cast<const char*>(X),
+                                             nb, xsb, csplit, N, s);
+            };
+            if (of == FMT_DD) {
+                if (xf == FMT_DD) go(k_combine_sb4<FMT_DD, FMT_DD>);
+                else if (xf == FMT_C64) go(k_combine_sb4<FMT_C64, FMT_DD>);
+                else go(k_combine_sb4<FMT_C128, FMT_DD>);
+            } else {
+                if (xf == FMT_DD) go(k_combine_sb4<FMT_DD, FMT_C128>);
+                else if (xf == FMT_C64) go(k_combine_sb4<FMT_C64, FMT_C128>);
+                else go(k_combine_sb4<FMT_C128, FMT_C128>);
+            }
+            L.post();
+            return;
+        }
         if (of == FMT_DD) {
             if (xf == FMT_DD) combine_dd_go<FMT_DD, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
             else if (xf == FMT_C64) combine_dd_go<FMT_C64, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
