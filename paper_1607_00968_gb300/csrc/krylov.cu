@@ -392,10 +392,31 @@ __device__ __forceinline__ void ld4(const char* b, long long plane, long long e0
     }
 }
 
-// Gram of groups of four: thread (g, r) accumulates the 4 x 4 block
-// conj(X_i[node][g*4+a]) Y[node][g*4+b] over the nodes n0 + r, n0 + r + R, ...
-// of its CTA's chunk (R = 128 / G replicas), loading the next node while it
-// works on the current one; replicas are added in FP64 in shared memory and
+// The same for two columns (e0 even).
+template <int F>
+__device__ __forceinline__ void ld2(const char* b, long long plane, long long e0, float4 (&v)[2]) {
+    if constexpr (F == FMT_DD) {
+        const float4 h = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + e0);
+        const float4 l = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(b) + plane + e0);
+        v[0] = make_float4(h.x, l.x, h.y, l.y);
+        v[1] = make_float4(h.z, l.z, h.w, l.w);
+    } else if constexpr (F == FMT_C64) {
+        const float4 a = *reinterpret_cast<const float4*>(reinterpret_cast<const c64*>(b) + e0);
+        v[0] = make_float4(a.x, 0.f, a.y, 0.f);
+        v[1] = make_float4(a.z, 0.f, a.w, 0.f);
+    } else {
+        const c128* p = reinterpret_cast<const c128*>(b) + e0;
+        v[0] = split_c(p[0]);
+        v[1] = split_c(p[1]);
+    }
+}
+
+// Gram of groups of four: thread (g, h, r) accumulates rows a = 2h, 2h+1 of
+// the 4 x 4 block conj(X_i[node][g*4+a]) Y[node][g*4+b] over the nodes
+// n0 + r, n0 + r + R, ... of its CTA's chunk (R = 128 / (2G) replicas),
+// loading the next node while it works on the current one (eight complex
+// double-float accumulators per thread keep the register count near 100, so
+// five CTAs share an SM); replicas are added in FP64 in shared memory and
 // each CTA writes one partial slot (layout of k_gram).
 template <int XF, int YF>
 __global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, long long xstride,
@@ -403,34 +424,38 @@ __global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, lo
                                                    int chunks, c128* __restrict__ partial) {
     extern __shared__ double2 red4[];              // R x G x 16
     const int G = s / 4;
-    const int R = 128 / G;
-    const int g = threadIdx.x % G, r = threadIdx.x / G;
+    const int T = 2 * G;                           // threads per replica
+    const int R = 128 / T;
+    const int q = threadIdx.x % T, r = threadIdx.x / T;
+    const int g = q >> 1, h = q & 1;
     const bool active = r < R;
-    const int i = blockIdx.y;
+    // block index fastest: the nb CTAs of one node chunk run side by side and
+    // share that chunk of Y through L2
+    const int i = blockIdx.x, chunk = blockIdx.y, nb = gridDim.x;
     const char* Xi = X + (long long)i * xstride;
     const long long plane = N * s;
     const long long per = (N + chunks - 1) / chunks;
-    const long long n0 = (long long)blockIdx.x * per;
+    const long long n0 = (long long)chunk * per;
     const long long n1 = n0 + per < N ? n0 + per : N;
-    float S[4][4][2], Lc[4][4][2];
+    float S[2][4][2], Lc[2][4][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) S[a][b][0] = S[a][b][1] = Lc[a][b][0] = Lc[a][b][1] = 0.f;
-    float4 xc[4], yc[4], xn[4], yn[4];
+    float4 xc[2], yc[4], xn[2], yn[4];
     long long n = n0 + r;
     if (active && n < n1) {
-        ld4<XF>(Xi, plane, n * s + g * 4, xc);
+        ld2<XF>(Xi, plane, n * s + g * 4 + 2 * h, xc);
         ld4<YF>(Y, plane, n * s + g * 4, yc);
     }
     for (; active && n < n1; n += R) {
         const long long nn = n + R;
         if (nn < n1) {
-            ld4<XF>(Xi, plane, nn * s + g * 4, xn);
+            ld2<XF>(Xi, plane, nn * s + g * 4 + 2 * h, xn);
             ld4<YF>(Y, plane, nn * s + g * 4, yn);
         }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const float4 x = xc[a], y = yc[b];
@@ -441,22 +466,24 @@ __global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, lo
                 dd_mac(S[a][b][1], Lc[a][b][1], -x.z, -x.w, y.x, y.y);
             }
 #pragma unroll
-        for (int a = 0; a < 4; ++a) { xc[a] = xn[a]; yc[a] = yn[a]; }
+        for (int a = 0; a < 2; ++a) xc[a] = xn[a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) yc[b] = yn[b];
     }
     const int E1 = G * 16;
     if (active)
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-                red4[(long long)(r * G + g) * 16 + a * 4 + b] =
+                red4[(long long)r * E1 + g * 16 + (2 * h + a) * 4 + b] =
                     make_double2(f2d_bits(S[a][b][0]) + f2d_bits(Lc[a][b][0]),
                                  f2d_bits(S[a][b][1]) + f2d_bits(Lc[a][b][1]));
     __syncthreads();
-    c128* out = partial + ((long long)blockIdx.x * gridDim.y + i) * E1;
+    c128* out = partial + ((long long)chunk * nb + i) * E1;
     for (int e = threadIdx.x; e < E1; e += blockDim.x) {
         double re = 0.0, im = 0.0;
-        for (int q = 0; q < R; ++q) { re += red4[(long long)q * E1 + e].x; im += red4[(long long)q * E1 + e].y; }
+        for (int k = 0; k < R; ++k) { re += red4[(long long)k * E1 + e].x; im += red4[(long long)k * E1 + e].y; }
         out[e] = mk(re, im);
     }
 }
@@ -807,10 +834,10 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
     dim3 grid(chunks, nb);
     const bool dd = emulate && gram_dd_ok(s, sb);
     L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
-    if (dd && sb == 4 && s % 4 == 0 && s <= 512) {
+    if (dd && sb == 4 && s % 4 == 0 && s <= 256) {
         // groups of four: 128-thread CTAs, about three per SM in one wave
         const int G4 = s / 4;
-        const int R4 = 128 / G4;
+        const int R4 = 128 / (2 * G4);
         const long long xsb = xstride * fmt_bytes(xf);
         const size_t sm4 = (size_t)R4 * G4 * 16 * sizeof(double2);
         const char* Xb = static_cast<const char*>(X);
@@ -823,7 +850,7 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
             int ch = (int)(tiles < want ? tiles : want);
             if (ch > chunks) ch = chunks;          // the partial buffer holds gram_chunks() slots
             if (ch < 1) ch = 1;
-            kern<<<dim3(ch, nb), 128, sm4, L.st>>>(Xb, xsb, Yb, N, s, ch, partial);
+            kern<<<dim3(nb, ch), 128, sm4, L.st>>>(Xb, xsb, Yb, N, s, ch, partial);
             chunks = ch;
         };
         if (xf == FMT_DD && yf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_DD>);
