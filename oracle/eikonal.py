@@ -85,8 +85,9 @@ def local_solve(i, multi, shape, h, t0, p0, m, tau1, known, choices, strides=Non
     """Godunov solve at flat node i from known neighbours (reading E2).
     Returns (tau1_i, choice tuple) or (inf, None) when no neighbour is known."""
     d = len(shape)
-    ti0 = t0[i]
-    # candidate terms alpha * x - beta per axis and direction
+    t0h = t0[i] / h
+    # candidate terms alpha * x - beta per axis and direction:
+    # alpha = tau0_i / h +- p0, beta = (tau0_i / h) tau1_nb
     cand = [[None, None, None] for _ in range(d)]
     if strides is None:
         strides = _strides(shape)
@@ -95,10 +96,10 @@ def local_solve(i, multi, shape, h, t0, p0, m, tau1, known, choices, strides=Non
         pa = p0[a][i]
         if k > 0 and known[i - strides[a]]:
             nb = i - strides[a]
-            cand[a][1] = (ti0 / h + pa, ti0 * tau1[nb] / h)
+            cand[a][1] = (t0h + pa, t0h * tau1[nb])
         if k < shape[a] - 1 and known[i + strides[a]]:
             nb = i + strides[a]
-            cand[a][2] = (ti0 / h - pa, ti0 * tau1[nb] / h)
+            cand[a][2] = (t0h - pa, t0h * tau1[nb])
     if all(cand[a][1] is None and cand[a][2] is None for a in range(d)):
         return math.inf, None
     mi = m[i]
