@@ -278,6 +278,39 @@ def timed_steps(torch, solvers, Qd, steps, stream):
 # the other configurations (small 2D, 3D, uneven batch)
 # --------------------------------------------------------------------------
 
+def eikonal_measure(helm, torch, m, h, ns):
+    """Factored-eikonal fast marching (Sec. 2.5) for ns sources on the top
+    row of model m, then one J v and one J^T w over all of them; one untimed
+    warm-up call of each, CUDA events around the timed calls."""
+    shape = m.shape
+    sources = [(0, int(x)) for x in np.linspace(1, shape[1] - 2, ns).round()]
+    ek = helm.Eikonal(shape, h, ns_max=ns)
+    v = torch.ones(m.size, dtype=torch.float64, device="cuda")
+    w = torch.ones((ns, m.size), dtype=torch.float64, device="cuda")
+    ek.forward(m, sources, outputs=())
+    ek.jv(v)
+    ek.jtw(w)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    ek.forward(m, sources, outputs=())
+    ev[1].record(stream)
+    ek.jv(v)
+    ev[2].record(stream)
+    ek.jtw(w)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    f_ms, jv_ms, jtw_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+    ek.close()
+    return {"value": ns / (f_ms / 1e3), "unit": "sources/s (fast marching)", "sources": ns,
+            "nodes": int(m.size), "forward_ms": round(f_ms, 2), "us_per_node_per_source":
+            round(f_ms * 1e3 / m.size, 3), "jv_ms": round(jv_ms, 3), "jtw_ms": round(jtw_ms, 3),
+            "what": "factored eikonal, first-order Godunov upwind, fast marching per source (one "
+                    "warp each, serial heap order), sensitivities by wavefront-parallel "
+                    "substitution; FP64 marching, single-precision tau1 for the products"}
+
+
 def run_other(args):
     import torch
     from paper_1607_00968_gb300 import helm, inputs
@@ -519,6 +552,11 @@ def main():
         for S in ws:
             S.close()
 
+    # ---------------- factored eikonal on the same model (Sec. 2.5) ----------------
+    eik = None
+    if not args.no_plain:
+        eik = eikonal_measure(helm, torch, probs[0].m, probs[0].h, NSRC)
+
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -549,7 +587,7 @@ def main():
                              ((args.restart + 1) * Q.nbytes / 1e9),
                        "parallelism": "dp%d (independent models per rank)" % world},
             "cycles_per_frequency": iters, "max_relres": relres,
-            "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg,
+            "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg, "eikonal": eik,
             "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,

@@ -367,6 +367,50 @@ const char* helm_profile_kernel_name(int kid);
 helm_status helm_profile_read(helm_ctx* ctx, int kid, double* time_ms, long long* launches,
                               double* bytes, double* flops);
 
+/* ---------------------------------------------------------------------
+ * Factored eikonal equation and its sensitivities (Sec. 2.5: Eq.
+ * factoredeikonal discretised by the first-order factored upwind scheme of
+ * Eq. Gudonov / Eq. FOfactoredD, solved by the fast marching algorithm;
+ * sensitivities by Eq. Sensitivity / Sensitivity2).  tau = tau0 tau1 with
+ * tau0 = |x - x_s|; m is the squared slowness (the Helmholtz m) on the same
+ * node grid: (n[k] + 1) nodes per axis, x1 fastest.  One fast marching per
+ * source (ordering: least tau0 tau1 first, ties by node index); the local
+ * solve is the Godunov equation solved exactly from accepted neighbours (the
+ * least root consistent with the max{}); the source node holds
+ * tau1 = sqrt(m_s).  The workspace keeps, per source, tau1 in single
+ * precision, the chosen derivative per node and the fast-marching wavefront
+ * levels, from which J v and J^T w are applied by forward / backward
+ * substitution in fast-marching order (Eq. Sensitivity2 is lower triangular
+ * in that order).  All calls run on the workspace's stream and return after
+ * synchronising it.
+ * ------------------------------------------------------------------- */
+typedef struct helm_eik helm_eik;
+
+/* Workspace for up to ns_max sources on a dim-dimensional grid of n[k] cells
+   per axis (x1, x2[, x3]) with spacing h (metres).  Device memory: about
+   (46 N + 16) bytes per source, N = number of nodes.  HELM_ERR_ARG on bad
+   sizes, HELM_ERR_NOMEM when the allocation fails. */
+helm_status helm_eik_create(int dim, const int* n, double h, int ns_max, void* cuda_stream,
+                            helm_eik** out);
+/* Fast marching for ns <= ns_max sources.  m: device, N doubles (positive).
+   src: host, ns x dim node indices (x1, x2[, x3]) per source, inside the
+   grid.  Optional device outputs (NULL to skip), each ns x N, source-major:
+   tau_out (travel time tau0 tau1, FP64), tau1_out (FP64), order_out (node of
+   each acceptance step, int32), dir_out (per node: 2 bits per axis from the
+   slowest axis (x3 in 3D, x2 in 2D) in the low bits, 1 backward / 2 forward
+   derivative, 0xFF at the source).  HELM_ERR_NOMEM if a heap would overflow
+   (not met on a connected grid), HELM_ERR_BREAKDOWN if a node is unreached. */
+helm_status helm_eik_forward(helm_eik* e, const double* m, const int* src, int ns, double* tau_out,
+                             double* tau1_out, int* order_out, unsigned char* dir_out);
+/* z (device, ns x N) = J_s v for every source of the last forward call,
+   J_s = d tau1 / d m (Eq. Sensitivity), v: device, N doubles. */
+helm_status helm_eik_jv(helm_eik* e, const double* v, double* z);
+/* y (device, ns x N) = J_s^T w_s, w: device, ns x N doubles. */
+helm_status helm_eik_jtw(helm_eik* e, const double* w, double* y);
+/* Last error message of the workspace ("" if none). */
+const char* helm_eik_last_error(const helm_eik* e);
+void helm_eik_destroy(helm_eik* e);
+
 #ifdef __cplusplus
 }
 #endif

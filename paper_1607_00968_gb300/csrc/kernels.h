@@ -1,6 +1,7 @@
 // Host-side launchers of the libhelm kernels (instantiated in mg.cu and
 // krylov.cu, called by the solver driver in solver.cu).
 #pragma once
+#include <string>
 #include "common.cuh"
 
 namespace helm {
@@ -207,5 +208,8 @@ void launch_fill_random_f(const Launch& L, void* X, int of, long long N, int s, 
                           unsigned long long seed);
 
 void launch_zero(const Launch& L, void* p, size_t bytes);
+
+// the message helm_last_error(NULL) returns on this thread
+void set_thread_error(const std::string& msg);
 
 }  // namespace helm

@@ -194,6 +194,12 @@ struct helm_ctx {
 
 namespace {
 
+}  // namespace
+
+void helm::set_thread_error(const std::string& msg) { g_thread_error = msg; }
+
+namespace {
+
 helm_status fail(helm_ctx* c, helm_status s, const std::string& msg) {
     if (c) c->err = msg;
     g_thread_error = msg;

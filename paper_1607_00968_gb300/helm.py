@@ -32,7 +32,8 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_learned_blob_bytes", "helm_learned_layer", "helm_conv3x3", "helm_conv3x3_wgrad",
            "helm_conv3x3_flip", "helm_adam", "helm_learned_input", "helm_learned_target",
            "helm_learned_loss", "helm_fields_to_half", "helm_fwi_jv", "helm_fwi_jtw",
-           "helm_fwi_gradient"]
+           "helm_fwi_gradient", "helm_eik_create", "helm_eik_forward", "helm_eik_jv", "helm_eik_jtw",
+           "helm_eik_last_error", "helm_eik_destroy"]
 
 
 class HelmParams(ctypes.Structure):
@@ -111,6 +112,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_fwi_jv": (i, [vp, vp, i, i, vp, vp, i, d, vp]),
         "helm_fwi_jtw": (i, [vp, vp, i, i, vp, vp, i, d, vp]),
         "helm_fwi_gradient": (i, [vp, vp, i, vp, vp, i, d, i, vp, P(d), vp]),
+        "helm_eik_create": (i, [i, P(i), d, i, vp, P(vp)]),
+        "helm_eik_forward": (i, [vp, vp, P(i), i, vp, vp, vp, vp]),
+        "helm_eik_jv": (i, [vp, vp, vp]),
+        "helm_eik_jtw": (i, [vp, vp, vp]),
+        "helm_eik_last_error": (ctypes.c_char_p, [vp]),
+        "helm_eik_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -401,3 +408,90 @@ class Solver:
         out = np.zeros((n, K), dtype=np.complex128)
         self._check(self.lib.helm_get_operator(self.ctx, level, out.ctypes.data_as(ctypes.c_void_p)))
         return out
+
+
+class Eikonal:
+    """Factored-eikonal fast marching and its sensitivities on the GPU
+    (helm_eik_*).
+
+    shape: node shape in numpy order (x1 last), as Solver's m; h: spacing;
+    ns_max: most sources per forward call.  Sources are node multi-indices in
+    numpy order; m is the squared slowness (numpy or torch, node shape)."""
+
+    def __init__(self, shape, h: float, ns_max: int, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libhelm needs a CUDA device")
+        self.lib = load()
+        self.torch = torch
+        self.shape = tuple(int(n) for n in shape)
+        self.d = len(self.shape)
+        if self.d not in (2, 3):
+            raise ValueError("2D or 3D node shape")
+        self.N = int(np.prod(self.shape))
+        cells = (ctypes.c_int * 3)(*([n - 1 for n in reversed(self.shape)] + [0] * (3 - self.d)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        e = ctypes.c_void_p()
+        st = self.lib.helm_eik_create(self.d, cells, float(h), int(ns_max),
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(e))
+        if st != HELM_OK:
+            raise HelmError(st, self.lib.helm_last_error(None).decode())
+        self.e = e
+        self.ns = 0
+
+    def _check(self, st):
+        if st != HELM_OK:
+            raise HelmError(st, self.lib.helm_eik_last_error(self.e).decode())
+
+    def forward(self, m, sources, outputs=("tau", "tau1", "order", "dir")):
+        """Fast marching for every source; returns a dict of the requested
+        device outputs, each (ns, N): tau, tau1 (float64), order (int32),
+        dir (uint8)."""
+        torch = self.torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        mt = torch.as_tensor(np.ascontiguousarray(m) if isinstance(m, np.ndarray) else m)
+        mt = mt.to(device=dev, dtype=torch.float64).contiguous().reshape(-1)
+        if mt.numel() != self.N:
+            raise ValueError("m must have the node shape")
+        ns = len(sources)
+        src = (ctypes.c_int * (ns * self.d))()
+        for b, sidx in enumerate(sources):
+            for k in range(self.d):                       # ABI order (x1, x2[, x3])
+                src[b * self.d + k] = int(sidx[self.d - 1 - k])
+        out = {}
+        kinds = {"tau": torch.float64, "tau1": torch.float64, "order": torch.int32, "dir": torch.uint8}
+        for k in outputs:
+            out[k] = torch.empty((ns, self.N), dtype=kinds[k], device=dev)
+        self._m = mt
+        self._check(self.lib.helm_eik_forward(self.e, _ptr(mt), src, ns, _ptr(out.get("tau")),
+                                              _ptr(out.get("tau1")), _ptr(out.get("order")),
+                                              _ptr(out.get("dir"))))
+        self.ns = ns
+        return out
+
+    def jv(self, v):
+        """z (ns, N) = J_s v for the sources of the last forward call."""
+        torch = self.torch
+        vt = torch.as_tensor(v).to(device="cuda", dtype=torch.float64).contiguous().reshape(-1)
+        z = torch.empty((self.ns, self.N), dtype=torch.float64, device=vt.device)
+        self._check(self.lib.helm_eik_jv(self.e, _ptr(vt), _ptr(z)))
+        return z
+
+    def jtw(self, w):
+        """y (ns, N) = J_s^T w_s, w of shape (ns, N)."""
+        torch = self.torch
+        wt = torch.as_tensor(w).to(device="cuda", dtype=torch.float64).contiguous()
+        y = torch.empty((self.ns, self.N), dtype=torch.float64, device=wt.device)
+        self._check(self.lib.helm_eik_jtw(self.e, _ptr(wt), _ptr(y)))
+        return y
+
+    def close(self):
+        if getattr(self, "e", None):
+            self.lib.helm_eik_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
