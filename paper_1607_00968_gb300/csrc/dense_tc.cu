@@ -6,11 +6,17 @@
 //     C' (nc x 2s) = A' (nc x 2nc) B' (2nc x 2s),
 // A' = the complex inverse viewed as interleaved (re, im) floats,
 // B' rows 2k = [Re f_k, Im f_k], 2k+1 = [-Im f_k, Re f_k], so that
-// C' = [Re u | Im u].  A' is rounded to tf32 once at set-up; the product
-// runs on mma.sync m16n8k8 tf32 tiles with FP32 accumulation (optionally
-// three products on hi/lo tf32 splits for FP32-class accuracy), fed by a
-// 3-stage cp.async pipeline, with the K range split over CTAs so that the
-// ~nc/128 row tiles fill the 152 SMs; a second kernel adds the K slices.
+// C' = [Re u | Im u].  The default product stores A' in FP16 (11
+// significant bits, the tf32 class, half the bytes of the matrix that is
+// streamed from HBM every cycle), scaled at set-up by a power of two so
+// that max |A'| = 2^13, and B' in FP16 with a power-of-two scale per
+// right-hand side; it runs on mma.sync m16n8k16 f16 tiles with FP32
+// accumulation, fed by a 4-stage cp.async pipeline, and the reduction of the
+// K slices removes the scales exactly.  The FP32-class option keeps A' in
+// FP32 and runs three mma.sync m16n8k8 tf32 products on hi/lo splits.  The K
+// range is split over CTAs so that the ~nc/128 row tiles fill the 152 SMs.
+#include <cuda_fp16.h>
+
 #include "kernels.h"
 
 namespace helm {
@@ -208,6 +214,213 @@ __global__ void k_build_aprime(const c128* __restrict__ Minv, int nc, float* __r
     Ap[e] = round_tf32 ? tf32_rna(v) : v;
 }
 
+// ---------------------------------------------------------------------------
+// FP16 path
+// ---------------------------------------------------------------------------
+constexpr int HBM_ = 128, HBN = 128, HBK = 32, HST = 4;   // tile and stages (K in halves)
+constexpr int HLD = HBK + 8;                                // padded row: ldmatrix without conflicts
+
+__device__ __forceinline__ void mma_f16(float* d, const unsigned int* a, const unsigned int* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ void ldsm4(unsigned int* r, const void* p) {
+    unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+// power of two p with m * p <= 2^13 < 2 m p (1 for m = 0 or not finite)
+__device__ __forceinline__ float pow2_scale(float mx) {
+    if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+    int e;
+    frexpf(mx, &e);                    // mx = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, 13 - e);
+}
+
+// max |re|, |im| over the nc x nc inverse, into *out (as float bits; the
+// values are >= 0 so integer max orders them)
+__global__ void k_absmax_c128(const c128* __restrict__ M, long long n, unsigned int* out) {
+    float mx = 0.f;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        c128 z = M[e];
+        mx = fmaxf(mx, fmaxf(fabsf((float)z.re), fabsf((float)z.im)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+// A'_h[i][2k + {0,1}] = half(scale (Re, Im) Minv[i][k]), scale = pow2_scale(max);
+// the scale is stored after the nc x Kp halves
+__global__ void k_build_aprime_h(const c128* __restrict__ Minv, int nc, __half* __restrict__ Ap, int Kp,
+                                 const unsigned int* __restrict__ mxbits) {
+    const float sc = pow2_scale(__uint_as_float(*mxbits));
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e == 0) *reinterpret_cast<float*>(Ap + (size_t)nc * Kp) = sc;
+    if (e >= (long long)nc * Kp) return;
+    int i = (int)(e / Kp), c = (int)(e - (long long)i * Kp);
+    float v = 0.f;
+    if (c < 2 * nc) {
+        c128 z = Minv[(size_t)i * nc + (c >> 1)];
+        v = __double2float_rn((c & 1) ? z.im : z.re) * sc;
+    }
+    Ap[e] = __float2half_rn(v);
+}
+
+// per right-hand side j: scale_j = pow2_scale(max_k max(|Re f_kj|, |Im f_kj|))
+__global__ void __launch_bounds__(256) k_colscale(const c64* __restrict__ f, int nc, int s, float* __restrict__ scale) {
+    const int j = blockIdx.x;
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        c64 z = f[(size_t)k * s + j];
+        mx = fmaxf(mx, fmaxf(fabsf(z.re), fabsf(z.im)));
+    }
+    __shared__ float red[8];
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+        scale[j] = pow2_scale(fmaxf(mx, red[0]));
+    }
+}
+
+// B'^T as halves, Bt[n][k] (k contiguous), n < ldb, k < Kp, with column scales:
+// column n < s holds [Re f; -Im f] interleaved by k, column s + n [Im f; Re f]
+__global__ void k_build_bt_h(const c64* __restrict__ f, int nc, int s, const float* __restrict__ scale,
+                             __half* __restrict__ Bt, int Kp, int ldb) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)ldb * Kp) return;
+    int n = (int)(e / Kp), k = (int)(e - (long long)n * Kp);
+    int kk = k >> 1, odd = k & 1;
+    float v = 0.f;
+    if (kk < nc && n < 2 * s) {
+        int j = n < s ? n : n - s;
+        c64 z = f[(size_t)kk * s + j];
+        if (!odd) v = n < s ? z.re : z.im;
+        else v = n < s ? -z.im : z.re;
+        v *= scale[j];
+    }
+    Bt[e] = __float2half_rn(v);
+}
+
+// P[ks][row][col] = sum over this CTA's K slice of A'_h[row][k] Bt[col][k].
+// 8 warps: 2 along M (64 rows) x 4 along N (32 columns); per k16 step a warp
+// loads 4 A and 4 B fragments with ldmatrix and issues 16 mma.
+__global__ void __launch_bounds__(256) k_dense_f16(const __half* __restrict__ A, int lda, int M,
+                                                    const __half* __restrict__ Bt, int kchunk, int Kp,
+                                                    float* __restrict__ P) {
+    extern __shared__ __align__(16) __half hsm[];
+    __half* As = hsm;                               // HST x HBM_ x HLD
+    __half* Bs = hsm + HST * HBM_ * HLD;            // HST x HBN x HLD
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int m0 = blockIdx.x * HBM_, n0 = blockIdx.z * HBN, ks = blockIdx.y;
+    const int k0 = ks * kchunk;
+    const int k1 = min(Kp, k0 + kchunk);
+    const int nk = k1 > k0 ? (k1 - k0) / HBK : 0;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    auto load_stage = [&](int stage, int kt) {
+        const int kk = k0 + kt * HBK;
+        __half* as = As + stage * HBM_ * HLD;
+        __half* bs = Bs + stage * HBN * HLD;
+        // 128 rows x 32 halves = 512 chunks of 16 B per operand: two per thread
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            int idx = tid + c * 256;
+            int r = idx >> 2, c8 = idx & 3;
+            int grow = m0 + r;
+            const __half* src = A + (size_t)(grow < M ? grow : M - 1) * lda + kk + c8 * 8;
+            cp_async16(as + r * HLD + c8 * 8, src, grow < M ? 16 : 0);
+            const __half* srcb = Bt + (size_t)(n0 + r) * Kp + kk + c8 * 8;
+            cp_async16(bs + r * HLD + c8 * 8, srcb, 16);
+        }
+    };
+#pragma unroll
+    for (int st = 0; st < HST - 1; ++st) {
+        if (st < nk) load_stage(st, st);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < nk; ++kt) {
+        cp_async_wait<HST - 2>();
+        __syncthreads();
+        int nxt = kt + HST - 1;
+        if (nxt < nk) load_stage(nxt % HST, nxt);
+        cp_async_commit();
+        const __half* as = As + (kt % HST) * HBM_ * HLD;
+        const __half* bs = Bs + (kt % HST) * HBN * HLD;
+#pragma unroll
+        for (int k16 = 0; k16 < HBK / 16; ++k16) {
+            unsigned int af[4][4], bf[4][2];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+                ldsm4(af[mt], as + (wm * 64 + mt * 16 + (lane & 15)) * HLD + k16 * 16 + (lane >> 4) * 8);
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {
+                // two n8 tiles per x4: matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+                unsigned int r4[4];
+                const int nrow = wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int kcol = k16 * 16 + ((lane >> 3) & 1) * 8;
+                ldsm4(r4, bs + nrow * HLD + kcol);
+                bf[2 * np][0] = r4[0];
+                bf[2 * np][1] = r4[1];
+                bf[2 * np + 1][0] = r4[2];
+                bf[2 * np + 1][1] = r4[3];
+            }
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) mma_f16(acc[mt][nt], af[mt], bf[nt]);
+        }
+    }
+    cp_async_wait<0>();
+    const int g = lane >> 2, t = lane & 3;
+    const int ldp = gridDim.z * HBN;
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            int row = m0 + wm * 64 + mt * 16 + g;
+            int col = n0 + wn * 32 + nt * 8 + 2 * t;
+            float* p = P + ((size_t)ks * M) * ldp;
+            if (row < M) {
+                p[(size_t)row * ldp + col] = acc[mt][nt][0];
+                p[(size_t)row * ldp + col + 1] = acc[mt][nt][1];
+            }
+            if (row + 8 < M) {
+                p[(size_t)(row + 8) * ldp + col] = acc[mt][nt][2];
+                p[(size_t)(row + 8) * ldp + col + 1] = acc[mt][nt][3];
+            }
+        }
+}
+
+// u[row][j] = (sum over K slices of C') / (scale_A scale_j)
+__global__ void k_reduce_cprime_h(const float* __restrict__ P, int KS, int M, int ldp, int s,
+                                  const float* __restrict__ ascale, const float* __restrict__ bscale,
+                                  c64* __restrict__ u) {
+    long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)M * s) return;
+    int row = (int)(e / s), j = (int)(e - (long long)row * s);
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < KS; ++k) {
+        const float* p = P + ((size_t)k * M + row) * ldp;
+        re += p[j];
+        im += p[s + j];
+    }
+    const float inv = 1.f / (*ascale * bscale[j]);      // a power of two: exact
+    u[e] = mk(re * inv, im * inv);
+}
+
 }  // namespace
 
 int dense_tc_kpad(int nc) { return ((2 * nc + TBK - 1) / TBK) * TBK; }
@@ -234,14 +447,28 @@ int dense_tc_ksplit(int nc, int s) {
     return best;
 }
 size_t dense_tc_scratch_floats(int nc, int s) {
-    return (size_t)dense_tc_kpad(nc) * dense_tc_ldb(s) + (size_t)kMaxKSplit * nc * dense_tc_ldb(s);
+    // B' (FP32, or FP16 B'^T in the first half), the K-slice partials, the
+    // column scales of the FP16 path
+    return (size_t)dense_tc_kpad(nc) * dense_tc_ldb(s) + (size_t)kMaxKSplit * nc * dense_tc_ldb(s) +
+           (size_t)dense_tc_ldb(s);
 }
 
 void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, bool split3) {
     int Kp = dense_tc_kpad(nc);
     long long n = (long long)nc * Kp;
     L.pre(KID_SETUP, 0, 0);
-    k_build_aprime<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(Minv, nc, Ap, Kp, split3 ? 0 : 1);
+    if (split3) {
+        k_build_aprime<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(Minv, nc, Ap, Kp, 0);
+    } else {
+        // FP16 A' in the first half of the buffer, its scale and the max after it
+        __half* Ah = reinterpret_cast<__half*>(Ap);
+        unsigned int* mx = reinterpret_cast<unsigned int*>(Ah + (size_t)nc * Kp) + 1;
+        cudaMemsetAsync(mx, 0, sizeof(unsigned int), L.st);
+        long long nn = (long long)nc * nc;
+        long long blocks = (nn + 255) / 256;
+        k_absmax_c128<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, L.st>>>(Minv, nn, mx);
+        k_build_aprime_h<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(Minv, nc, Ah, Kp, mx);
+    }
     L.post();
 }
 
@@ -251,6 +478,30 @@ void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64
     float* Bp = scratch;
     float* P = scratch + (size_t)Kp * ldb;
     long long nb = (long long)Kp * ldb;
+    if (!split3) {
+        // FP16: column scales, B'^T, the product, the scaled reduction
+        const __half* Ah = reinterpret_cast<const __half*>(Ap);
+        const float* ascale = reinterpret_cast<const float*>(Ah + (size_t)nc * Kp);
+        float* bscale = P + (size_t)kMaxKSplit * nc * ldb;
+        __half* Bt = reinterpret_cast<__half*>(Bp);
+        L.pre(KID_LAYOUT, 2.0 * nb + 16.0 * nc * s, 0);
+        k_colscale<<<s, 256, 0, L.st>>>(f, nc, s, bscale);
+        k_build_bt_h<<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, bscale, Bt, Kp, ldb);
+        L.post();
+        int kchunk = ((Kp / HBK + KS - 1) / KS) * HBK;
+        dim3 grid((nc + HBM_ - 1) / HBM_, KS, ldb / HBN);
+        size_t smem = sizeof(__half) * (size_t)HST * (HBM_ + HBN) * HLD;
+        cudaFuncSetAttribute(k_dense_f16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        L.pre(KID_DENSE, 2.0 * nc * (double)Kp + 2.0 * nb + 4.0 * KS * nc * (double)ldb,
+              8.0 * nc * (double)nc * s);
+        k_dense_f16<<<grid, 256, smem, L.st>>>(Ah, Kp, nc, Bt, kchunk, Kp, P);
+        L.post();
+        L.pre(KID_LAYOUT, 4.0 * KS * nc * 2.0 * s + 8.0 * nc * s, 0);
+        k_reduce_cprime_h<<<(unsigned)(((long long)nc * s + 255) / 256), 256, 0, L.st>>>(P, KS, nc, ldb, s,
+                                                                                          ascale, bscale, u);
+        L.post();
+        return;
+    }
     L.pre(KID_LAYOUT, 4.0 * nb + 8.0 * nc * s, 0);
     if (split3) k_build_bprime<false><<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, Bp, ldb, Kp);
     else k_build_bprime<true><<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, Bp, ldb, Kp);

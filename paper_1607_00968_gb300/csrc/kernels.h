@@ -63,11 +63,14 @@ int dense_tc_kpad(int nc);
 int dense_tc_ldb(int s);
 int dense_tc_ksplit(int nc, int s);
 size_t dense_tc_scratch_floats(int nc, int s);
-// A' (nc x dense_tc_kpad(nc) floats): interleaved (re, im) of Minv in FP32,
-// rounded to tf32 unless split3 (the three-product solve splits it itself)
+// A' in a buffer of nc x dense_tc_kpad(nc) floats: interleaved (re, im) of
+// Minv; split3: FP32 (the three-product solve splits it itself); otherwise
+// FP16 scaled by a power of two (max |A'| = 2^13) in the first half, the
+// scale as a float right after it
 void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, bool split3);
 // u = Minv f for complex64 blocks (nc x s, node-major) from A'; split3: three
-// tf32 products on hi/lo splits (FP32-class accuracy) instead of one
+// tf32 products on hi/lo splits (FP32-class accuracy); otherwise one FP16
+// product (11 significant bits, scaled per right-hand side)
 void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
                      float* scratch, bool split3);
 
