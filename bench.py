@@ -42,7 +42,7 @@ DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
 # class, from six launches of one 5 Hz salt solve: reads match the
 # algorithmic count, about 40% of the written bytes are still in L2 when the
 # launch ends.  Valid while the kernel is unchanged.
-TRAFFIC_RATIO = {"combine_dd": (0.847, "profiles/traffic_salt2d_512x256_5hz.md")}
+TRAFFIC_RATIO = {}
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
 SOLVER = dict(pre=2, post=2, jacobi_w=0.8)

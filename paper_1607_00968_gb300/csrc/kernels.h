@@ -181,8 +181,11 @@ void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, cons
 
 // Same with the operands' formats (xstride in elements of X's format: 16
 // bytes for FMT_C128 and FMT_DD, 8 for FMT_C64).  FMT_DD needs emulate.
+// hi_only (both FMT_DD, groups of four): products of the hi parts in FP32,
+// for a first Gram-Schmidt pass whose error a double-float pass removes.
 void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xstride, const void* Y,
-                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate);
+                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate,
+                   bool hi_only = false);
 
 // out[node][g*sb+b] = beta*out + sign * sum_{i<nb} sum_a X_i[node][g*sb+a] C[i][g][a][b]
 // emulate: double-float arithmetic (needs csplit: scratch of nb*G*sb*sb float4

@@ -488,6 +488,64 @@ __global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, lo
     }
 }
 
+// First Gram-Schmidt pass of float-pair blocks: the same products from the
+// hi planes only, in FP32 (4 FMA per complex product; each thread sums its
+// nodes in FP32, replicas and chunks are added in FP64).  Its error, a few
+// 1e-6 of |X| |Y|, is removed by the second pass, whose coefficients are
+// computed in double-float arithmetic from the updated block.
+__global__ void __launch_bounds__(128) k_gram_sb4_hi(const char* __restrict__ X, long long xstride,
+                                                      const char* __restrict__ Y, long long N, int s,
+                                                      int chunks, c128* __restrict__ partial) {
+    extern __shared__ double2 red4[];
+    const int G = s / 4;
+    const int T = 2 * G;
+    const int R = 128 / T;
+    const int q = threadIdx.x % T, r = threadIdx.x / T;
+    const int g = q >> 1, h = q & 1;
+    const bool active = r < R;
+    const int i = blockIdx.x, chunk = blockIdx.y, nb = gridDim.x;
+    const float2* Xh = reinterpret_cast<const float2*>(X + (long long)i * xstride);
+    const float2* Yh = reinterpret_cast<const float2*>(Y);
+    const long long per = (N + chunks - 1) / chunks;
+    const long long n0 = (long long)chunk * per;
+    const long long n1 = n0 + per < N ? n0 + per : N;
+    float acc[2][4][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.f;
+    for (long long n = n0 + r; active && n < n1; n += R) {
+        const float4 xv = *reinterpret_cast<const float4*>(Xh + n * s + g * 4 + 2 * h);
+        const float4 y0 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4);
+        const float4 y1 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4 + 2);
+        const float xr[2] = {xv.x, xv.z}, xi[2] = {xv.y, xv.w};
+        const float yr[4] = {y0.x, y0.z, y1.x, y1.z}, yi[4] = {y0.y, y0.w, y1.y, y1.w};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                // conj(x) y
+                acc[a][b][0] = fmaf(xr[a], yr[b], fmaf(xi[a], yi[b], acc[a][b][0]));
+                acc[a][b][1] = fmaf(xr[a], yi[b], fmaf(-xi[a], yr[b], acc[a][b][1]));
+            }
+    }
+    const int E1 = G * 16;
+    if (active)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                red4[(long long)r * E1 + g * 16 + (2 * h + a) * 4 + b] =
+                    make_double2((double)acc[a][b][0], (double)acc[a][b][1]);
+    __syncthreads();
+    c128* out = partial + ((long long)chunk * nb + i) * E1;
+    for (int e = threadIdx.x; e < E1; e += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < R; ++k) { re += red4[(long long)k * E1 + e].x; im += red4[(long long)k * E1 + e].y; }
+        out[e] = mk(re, im);
+    }
+}
+
 // Block update for groups of four: thread (node, g) forms the four outputs
 // of its group, sum_i sum_a X_i[node][g*4+a] C[i][g][a][b], from X_i read
 // straight from global memory (the next block's values loaded ahead) and the
@@ -826,14 +884,19 @@ void gram_dd_dispatch(int xf, int yf, dim3 grid, size_t sm, cudaStream_t st, con
 }  // namespace
 
 void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xstride, const void* Y,
-                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
+                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate,
+                   bool hi_only) {
     int G = (s + sb - 1) / sb;
     long long E1 = (long long)G * sb * sb;
     int chunks = gram_chunks(N, nb, s);
     size_t smem = 2 * sizeof(c128) * (size_t)gram_tile_nodes(s) * s;
     dim3 grid(chunks, nb);
     const bool dd = emulate && gram_dd_ok(s, sb);
-    L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
+    const bool hi = hi_only && dd && sb == 4 && s % 4 == 0 && s <= 256 && xf == FMT_DD && yf == FMT_DD;
+    if (hi)   // FP32 products of the hi planes: 8 bytes per element and block
+        L.pre(KID_GRAM_HI, (nb + 1.0) * N * s * 8.0, 8.0 * nb * (double)N * s * sb);
+    else
+        L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
     if (dd && sb == 4 && s % 4 == 0 && s <= 256) {
         // groups of four: 128-thread CTAs, about three per SM in one wave
         const int G4 = s / 4;
@@ -853,7 +916,8 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
             kern<<<dim3(nb, ch), 128, sm4, L.st>>>(Xb, xsb, Yb, N, s, ch, partial);
             chunks = ch;
         };
-        if (xf == FMT_DD && yf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_DD>);
+        if (hi) go(k_gram_sb4_hi);
+        else if (xf == FMT_DD && yf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_DD>);
         else if (xf == FMT_DD) go(k_gram_sb4<FMT_DD, FMT_C128>);
         else if (yf == FMT_DD) go(k_gram_sb4<FMT_C128, FMT_DD>);
         else go(k_gram_sb4<FMT_C128, FMT_C128>);
@@ -887,7 +951,7 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
 
 void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
                  long long N, int s, int sb, c128* partial, c128* out, bool emulate) {
-    launch_gram_f(L, X, FMT_C128, nb, xstride, Y, FMT_C128, N, s, sb, partial, out, emulate);
+    launch_gram_f(L, X, FMT_C128, nb, xstride, Y, FMT_C128, N, s, sb, partial, out, emulate, false);
 }
 
 namespace {

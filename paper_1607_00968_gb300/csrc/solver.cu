@@ -664,8 +664,10 @@ void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
     const long long vs = N * s;
     for (int pass = 0; pass < 2; ++pass) {
         c128* H = pass == 0 ? H1 : H2;
+        // the first pass may use FP32 products of the hi parts: the second,
+        // double-float pass removes their error (its coefficients add to H)
         helm::launch_gram_f(c->L(), c->V, c->kfmt, nb, vs, Wp, c->kfmt, N, s, sb, c->partial, H,
-                            emulated(c));
+                            emulated(c), pass == 0 && c->kfmt == helm::FMT_DD);
         helm::launch_combine_f(c->L(), Wp, c->kfmt, 1.0, -1.0, c->V, c->kfmt, nb, vs, H, N, s, sb,
                                emulated(c), c->csplit);
     }
@@ -1759,7 +1761,7 @@ static const char* kKernelNames[helm::KID_COUNT] = {
     "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",
     "restrict_fine", "restrict_coarse", "prolong_add", "coarsest_dense", "gram", "gram_reduce",
     "combine", "layout", "random_fill", "setup", "gram_dd", "combine_dd", "conv3x3",
-    "conv3x3_wgrad"};
+    "conv3x3_wgrad", "gram_hi"};
 
 helm_status helm_profile_enable(helm_ctx* c, int enable) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
