@@ -294,7 +294,7 @@ struct GalOp {
 enum KernelId {
     KID_APPLY_FINE = 0, KID_APPLY_COARSE, KID_RESIDUAL, KID_JACOBI_FINE, KID_JACOBI_COARSE,
     KID_RESTRICT_FINE, KID_RESTRICT_COARSE, KID_PROLONG, KID_DENSE, KID_GRAM, KID_GRAM_REDUCE,
-    KID_COMBINE, KID_LAYOUT, KID_RANDOM, KID_SETUP, KID_GRAM_DD, KID_COMBINE_DD, KID_CONV, KID_CONV_WGRAD, KID_GRAM_HI, KID_COUNT
+    KID_COMBINE, KID_LAYOUT, KID_RANDOM, KID_SETUP, KID_GRAM_DD, KID_COMBINE_DD, KID_CONV, KID_CONV_WGRAD, KID_GRAM_HI, KID_COMBINE_HI, KID_COUNT
 };
 
 struct Profiler;  // host side, defined in solver.cu

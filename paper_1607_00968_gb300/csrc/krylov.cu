@@ -642,6 +642,72 @@ __global__ void __launch_bounds__(256) k_combine_sb4(char* __restrict__ out, dou
     }
 }
 
+// Second Gram-Schmidt update of float-pair blocks: its coefficients are the
+// small correction left by the first pass (a few 1e-6 of the block), so the
+// product sum_i sum_a X_i C_i is formed in FP32 from the hi planes of X and
+// of C (error ~1e-7 of a term that small: double-float class for the
+// result) and added to the float-pair output with TwoSum.  beta = 1.
+__global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, double sign,
+                                                         const char* __restrict__ X, int nb,
+                                                         long long xstride,
+                                                         const float4* __restrict__ Cs, long long N,
+                                                         int s) {
+    extern __shared__ float2 cs2[];                // nb x 4 x 4 x G, (re hi, im hi)
+    const int G = s / 4;
+    const int nc = nb * G * 16;
+    for (int idx = threadIdx.x; idx < nc; idx += blockDim.x) {
+        int i = idx / (G * 16), rem = idx - i * G * 16;
+        int g = rem / 16, ab = rem - g * 16;
+        const float4 c = Cs[idx];
+        cs2[(i * 16 + ab) * G + g] = make_float2(c.x, c.z);
+    }
+    __syncthreads();
+    const long long plane = N * s;
+    const long long total = N * G;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long node = t / G;
+        const int g = (int)(t - node * G);
+        const long long e0 = node * s + g * 4;
+        float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = 0; i < nb; ++i) {
+            const float4* xp = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(X + (long long)i * xstride) + e0);
+            const float4 x01 = xp[0], x23 = xp[1];
+            const float xr[4] = {x01.x, x01.z, x23.x, x23.z}, xi[4] = {x01.y, x01.w, x23.y, x23.w};
+            const float2* ci = cs2 + (long long)i * 16 * G + g;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const float2 c = ci[(a * 4 + b) * G];
+                    ar[b] = fmaf(xr[a], c.x, fmaf(-xi[a], c.y, ar[b]));
+                    ai[b] = fmaf(xr[a], c.y, fmaf(xi[a], c.x, ai[b]));
+                }
+        }
+        float2* o = reinterpret_cast<float2*>(out);
+        const float4 oh0 = reinterpret_cast<const float4*>(o + e0)[0], oh1 = reinterpret_cast<const float4*>(o + e0)[1];
+        const float4 ol0 = reinterpret_cast<const float4*>(o + plane + e0)[0],
+                     ol1 = reinterpret_cast<const float4*>(o + plane + e0)[1];
+        const float ohv[8] = {oh0.x, oh0.y, oh0.z, oh0.w, oh1.x, oh1.y, oh1.z, oh1.w};
+        const float olv[8] = {ol0.x, ol0.y, ol0.z, ol0.w, ol1.x, ol1.y, ol1.z, ol1.w};
+        float hv[8], lv[8];
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float d = sign < 0.0 ? -(q ? ai[b] : ar[b]) : (q ? ai[b] : ar[b]);
+                float t2, err;
+                two_sum(ohv[2 * b + q], d, t2, err);
+                err = __fadd_rn(err, olv[2 * b + q]);
+                two_sum(t2, err, hv[2 * b + q], lv[2 * b + q]);
+            }
+        reinterpret_cast<float4*>(o + e0)[0] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        reinterpret_cast<float4*>(o + e0)[1] = make_float4(hv[4], hv[5], hv[6], hv[7]);
+        reinterpret_cast<float4*>(o + plane + e0)[0] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        reinterpret_cast<float4*>(o + plane + e0)[1] = make_float4(lv[4], lv[5], lv[6], lv[7]);
+    }
+}
+
 constexpr int kCombineRows = 4;   // nodes per thread in the dd combine
 
 __global__ void k_split(const c128* __restrict__ C, float4* __restrict__ Cs, long long n) {
@@ -969,7 +1035,7 @@ void combine_dd_go(const Launch& L, int grid, size_t smem, void* out, double bet
 
 void launch_combine_f(const Launch& L, void* out, int of, double beta, double sign, const void* X,
                       int xf, int nb, long long xstride, const c128* C, long long N, int s, int sb,
-                      bool emulate, float4* csplit) {
+                      bool emulate, float4* csplit, bool hi_only) {
     const double xb = xf == FMT_C64 ? 8.0 : 16.0;
     if (emulate && csplit && combine_dd_ok(s, sb)) {
         const int T = (kThreads / s) * kCombineRows;
@@ -981,6 +1047,21 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
         L.pre(KID_LAYOUT, 32.0 * nc, 0);
         k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
         L.post();
+        if (hi_only && sb == 4 && s % 4 == 0 && xf == FMT_DD && of == FMT_DD && beta == 1.0 &&
+            (size_t)nb * G * 16 * sizeof(float2) <= 160 * 1024) {
+            L.pre(KID_COMBINE_HI, (double)N * s * (nb * 8.0 + 32.0), 8.0 * nb * (double)N * s * sb);
+            const long long total = N * (s / 4);
+            const size_t sm2 = (size_t)nb * G * 16 * sizeof(float2);
+            if (sm2 > 48 * 1024)
+                cudaFuncSetAttribute(k_combine_sb4_hi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+            long long want = (total + 255) / 256;
+            long long cap = (long long)resident_ctas(k_combine_sb4_hi, 256, sm2) * 152;
+            const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+            k_combine_sb4_hi<<<g4, 256, sm2, L.st>>>(static_cast<char*>(out), sign, static_cast<const char*>(X),
+                                                     nb, xstride * fmt_bytes(xf), csplit, N, s);
+            L.post();
+            return;
+        }
         L.pre(KID_COMBINE_DD, (double)N * s * (nb * xb + (beta != 0.0 ? 32.0 : 16.0)),
               8.0 * nb * (double)N * s * sb);
         const long long xsb = xstride * fmt_bytes(xf);
@@ -1039,7 +1120,7 @@ void launch_combine(const Launch& L, c128* out, double beta, double sign, const 
                     int nb, long long xstride, const c128* C, long long N, int s, int sb,
                     bool emulate, float4* csplit) {
     launch_combine_f(L, out, FMT_C128, beta, sign, X, sizeof(TX) == 4 ? FMT_C64 : FMT_C128, nb, xstride,
-                     C, N, s, sb, emulate, csplit);
+                     C, N, s, sb, emulate, csplit, false);
 }
 template void launch_combine<double>(const Launch&, c128*, double, double, const c128*, int,
                                      long long, const c128*, long long, int, int, bool, float4*);

@@ -668,8 +668,10 @@ void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
         // double-float pass removes their error (its coefficients add to H)
         helm::launch_gram_f(c->L(), c->V, c->kfmt, nb, vs, Wp, c->kfmt, N, s, sb, c->partial, H,
                             emulated(c), pass == 0 && c->kfmt == helm::FMT_DD);
+        // the second update's coefficients are the first pass's small error:
+        // on the float-pair basis its product may run in FP32 (hi parts)
         helm::launch_combine_f(c->L(), Wp, c->kfmt, 1.0, -1.0, c->V, c->kfmt, nb, vs, H, N, s, sb,
-                               emulated(c), c->csplit);
+                               emulated(c), c->csplit, pass == 1 && c->kfmt == helm::FMT_DD);
     }
 }
 
@@ -1761,7 +1763,7 @@ static const char* kKernelNames[helm::KID_COUNT] = {
     "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",
     "restrict_fine", "restrict_coarse", "prolong_add", "coarsest_dense", "gram", "gram_reduce",
     "combine", "layout", "random_fill", "setup", "gram_dd", "combine_dd", "conv3x3",
-    "conv3x3_wgrad", "gram_hi"};
+    "conv3x3_wgrad", "gram_hi", "combine_hi"};
 
 helm_status helm_profile_enable(helm_ctx* c, int enable) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
