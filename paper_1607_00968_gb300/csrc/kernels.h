@@ -197,12 +197,13 @@ void launch_combine(const Launch& L, c128* out, double beta, double sign, const 
 
 // Same with formats; an FMT_DD output or X needs emulate and
 // dd_formats_ok(s, sb), and an FMT_DD output beta in {0, 1}, sign = +-1.
-// hi_only (FMT_DD in and out, groups of four, beta = 1): the product in FP32
-// from the hi parts, for a second Gram-Schmidt update whose coefficients are
-// the small correction of a first pass; added to the pair output exactly.
+// hi_only (FMT_DD in and out, groups of four, beta = 1): out = base + sign X C
+// with the product in FP32 from the hi parts, for corrections whose
+// coefficients are small (a second Gram-Schmidt update, a QR factor near the
+// identity minus the identity); added to the pairs of base (null: out) exactly.
 void launch_combine_f(const Launch& L, void* out, int of, double beta, double sign, const void* X,
                       int xf, int nb, long long xstride, const c128* C, long long N, int s, int sb,
-                      bool emulate, float4* csplit, bool hi_only = false);
+                      bool emulate, float4* csplit, bool hi_only = false, const void* base = nullptr);
 
 // per-column squared 2-norms of X (N x s node-major): out[j] (FP64)
 long long colnorm_partial_elems(long long N, int s);

@@ -642,13 +642,14 @@ __global__ void __launch_bounds__(256) k_combine_sb4(char* __restrict__ out, dou
     }
 }
 
-// Second Gram-Schmidt update of float-pair blocks: its coefficients are the
-// small correction left by the first pass (a few 1e-6 of the block), so the
-// product sum_i sum_a X_i C_i is formed in FP32 from the hi planes of X and
-// of C (error ~1e-7 of a term that small: double-float class for the
-// result) and added to the float-pair output with TwoSum.  beta = 1.
-__global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, double sign,
-                                                         const char* __restrict__ X, int nb,
+// out = base + sign sum_i sum_a X_i C_i for float-pair blocks whose product
+// is a small correction (the second Gram-Schmidt update, whose coefficients
+// are the first pass's error, a few 1e-6 of the block; or the second QR
+// factor minus the identity): the product is formed in FP32 from the hi
+// planes of X and of C (error ~1e-7 of a term that small: double-float class
+// for the result) and added to the float pairs of base with TwoSum.
+__global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, const char* __restrict__ base,
+                                                         double sign, const char* __restrict__ X, int nb,
                                                          long long xstride,
                                                          const float4* __restrict__ Cs, long long N,
                                                          int s) {
@@ -685,9 +686,10 @@ __global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, 
                 }
         }
         float2* o = reinterpret_cast<float2*>(out);
-        const float4 oh0 = reinterpret_cast<const float4*>(o + e0)[0], oh1 = reinterpret_cast<const float4*>(o + e0)[1];
-        const float4 ol0 = reinterpret_cast<const float4*>(o + plane + e0)[0],
-                     ol1 = reinterpret_cast<const float4*>(o + plane + e0)[1];
+        const float2* bs = reinterpret_cast<const float2*>(base);
+        const float4 oh0 = reinterpret_cast<const float4*>(bs + e0)[0], oh1 = reinterpret_cast<const float4*>(bs + e0)[1];
+        const float4 ol0 = reinterpret_cast<const float4*>(bs + plane + e0)[0],
+                     ol1 = reinterpret_cast<const float4*>(bs + plane + e0)[1];
         const float ohv[8] = {oh0.x, oh0.y, oh0.z, oh0.w, oh1.x, oh1.y, oh1.z, oh1.w};
         const float olv[8] = {ol0.x, ol0.y, ol0.z, ol0.w, ol1.x, ol1.y, ol1.z, ol1.w};
         float hv[8], lv[8];
@@ -1035,7 +1037,7 @@ void combine_dd_go(const Launch& L, int grid, size_t smem, void* out, double bet
 
 void launch_combine_f(const Launch& L, void* out, int of, double beta, double sign, const void* X,
                       int xf, int nb, long long xstride, const c128* C, long long N, int s, int sb,
-                      bool emulate, float4* csplit, bool hi_only) {
+                      bool emulate, float4* csplit, bool hi_only, const void* base) {
     const double xb = xf == FMT_C64 ? 8.0 : 16.0;
     if (emulate && csplit && combine_dd_ok(s, sb)) {
         const int T = (kThreads / s) * kCombineRows;
@@ -1057,8 +1059,10 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
             long long want = (total + 255) / 256;
             long long cap = (long long)resident_ctas(k_combine_sb4_hi, 256, sm2) * 152;
             const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
-            k_combine_sb4_hi<<<g4, 256, sm2, L.st>>>(static_cast<char*>(out), sign, static_cast<const char*>(X),
-                                                     nb, xstride * fmt_bytes(xf), csplit, N, s);
+            k_combine_sb4_hi<<<g4, 256, sm2, L.st>>>(static_cast<char*>(out),
+                                                     static_cast<const char*>(base ? base : out), sign,
+                                                     static_cast<const char*>(X), nb,
+                                                     xstride * fmt_bytes(xf), csplit, N, s);
             L.post();
             return;
         }
@@ -1120,7 +1124,7 @@ void launch_combine(const Launch& L, c128* out, double beta, double sign, const 
                     int nb, long long xstride, const c128* C, long long N, int s, int sb,
                     bool emulate, float4* csplit) {
     launch_combine_f(L, out, FMT_C128, beta, sign, X, sizeof(TX) == 4 ? FMT_C64 : FMT_C128, nb, xstride,
-                     C, N, s, sb, emulate, csplit, false);
+                     C, N, s, sb, emulate, csplit, false, nullptr);
 }
 template void launch_combine<double>(const Launch&, c128*, double, double, const c128*, int,
                                      long long, const c128*, long long, int, int, bool, float4*);

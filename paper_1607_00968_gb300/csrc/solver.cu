@@ -773,9 +773,29 @@ helm_status block_qr(helm_ctx* c, c128* Win, int wfmt, c128* Vout, int nb, int s
             }
         out.R[g] = Rg;
     }
+    // The second factor is the identity up to the first pass's orthogonality
+    // error.  On the float-pair basis, when |T2 - I| <= 1e-7 everywhere,
+    // Vout = W2 + W2 (T2 - I) forms the correction in FP32 from hi parts
+    // (error <= ~1e-14 of W2, the double-float class) and adds it exactly.
+    bool near_identity = c->kfmt == helm::FMT_DD && sb == 4 && s % 4 == 0;
+    for (int g = 0; g < G && near_identity; ++g) {
+        const int n = std::min(sb, s - g * sb);
+        for (int a = 0; a < n && near_identity; ++a)
+            for (int b = 0; b < n; ++b) {
+                const cd v = hT[(size_t)g * sb * sb + a * sb + b] - (a == b ? cd(1.0) : cd(0.0));
+                if (!(std::abs(v) <= 1e-7)) { near_identity = false; break; }
+            }
+    }
+    if (near_identity)
+        for (int g = 0; g < G; ++g)
+            for (int a = 0; a < sb; ++a) hT[(size_t)g * sb * sb + a * sb + a] -= cd(1.0);
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
-    helm::launch_combine_f(c->L(), Vout, c->kfmt, 0.0, 1.0, c->W2, c->kfmt, 1, 0, dT, N, s, sb,
-                           emulated(c), c->csplit);
+    if (near_identity)
+        helm::launch_combine_f(c->L(), Vout, c->kfmt, 1.0, 1.0, c->W2, c->kfmt, 1, 0, dT, N, s, sb,
+                               emulated(c), c->csplit, true, c->W2);
+    else
+        helm::launch_combine_f(c->L(), Vout, c->kfmt, 0.0, 1.0, c->W2, c->kfmt, 1, 0, dT, N, s, sb,
+                               emulated(c), c->csplit);
     return HELM_OK;
 }
 
