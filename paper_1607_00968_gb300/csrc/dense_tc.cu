@@ -271,27 +271,32 @@ __global__ void k_build_aprime_h(const c128* __restrict__ Minv, int nc, __half* 
     Ap[e] = __float2half_rn(v);
 }
 
-// per right-hand side j: scale_j = pow2_scale(max_k max(|Re f_kj|, |Im f_kj|))
-__global__ void __launch_bounds__(256) k_colscale(const c64* __restrict__ f, int nc, int s, float* __restrict__ scale) {
-    const int j = blockIdx.x;
+// per right-hand side j: colmax[j] = max_k max(|Re f_kj|, |Im f_kj|) (float
+// bits; non-negative, so the integer max orders them).  Rows of f are read
+// whole (coalesced); each CTA reduces its rows per column in shared memory.
+__global__ void __launch_bounds__(256) k_colmax(const c64* __restrict__ f, int nc, int s,
+                                                unsigned int* __restrict__ colmax) {
+    __shared__ float red[256];
+    const int j0 = blockIdx.y * 256;                   // columns j0 .. j0 + sc - 1 (gridDim.y chunks)
+    const int sc = s - j0 < 256 ? s - j0 : 256;
+    const int jj = threadIdx.x % sc, sub = threadIdx.x / sc, per = 256 / sc;
     float mx = 0.f;
-    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
-        c64 z = f[(size_t)k * s + j];
-        mx = fmaxf(mx, fmaxf(fabsf(z.re), fabsf(z.im)));
-    }
-    __shared__ float red[8];
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    if (sub < per)
+        for (long long k = (long long)blockIdx.x * per + sub; k < nc; k += (long long)gridDim.x * per) {
+            c64 z = f[k * s + j0 + jj];
+            mx = fmaxf(mx, fmaxf(fabsf(z.re), fabsf(z.im)));
+        }
+    red[threadIdx.x] = sub < per ? mx : 0.f;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
-        scale[j] = pow2_scale(fmaxf(mx, red[0]));
+    if (sub == 0) {
+        for (int q = 1; q < per; ++q) mx = fmaxf(mx, red[q * sc + jj]);
+        atomicMax(colmax + j0 + jj, __float_as_uint(mx));
     }
 }
 
 // B'^T as halves, Bt[n][k] (k contiguous), n < ldb, k < Kp, with column scales:
 // column n < s holds [Re f; -Im f] interleaved by k, column s + n [Im f; Re f]
-__global__ void k_build_bt_h(const c64* __restrict__ f, int nc, int s, const float* __restrict__ scale,
+__global__ void k_build_bt_h(const c64* __restrict__ f, int nc, int s, const unsigned int* __restrict__ colmax,
                              __half* __restrict__ Bt, int Kp, int ldb) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)ldb * Kp) return;
@@ -303,7 +308,7 @@ __global__ void k_build_bt_h(const c64* __restrict__ f, int nc, int s, const flo
         c64 z = f[(size_t)kk * s + j];
         if (!odd) v = n < s ? z.re : z.im;
         else v = n < s ? -z.im : z.re;
-        v *= scale[j];
+        v *= pow2_scale(__uint_as_float(colmax[j]));
     }
     Bt[e] = __float2half_rn(v);
 }
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(256) k_dense_f16(const __half* __restrict__ A,
 
 // u[row][j] = (sum over K slices of C') / (scale_A scale_j)
 __global__ void k_reduce_cprime_h(const float* __restrict__ P, int KS, int M, int ldp, int s,
-                                  const float* __restrict__ ascale, const float* __restrict__ bscale,
+                                  const float* __restrict__ ascale, const unsigned int* __restrict__ colmax,
                                   c64* __restrict__ u) {
     long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)M * s) return;
@@ -417,7 +422,7 @@ __global__ void k_reduce_cprime_h(const float* __restrict__ P, int KS, int M, in
         re += p[j];
         im += p[s + j];
     }
-    const float inv = 1.f / (*ascale * bscale[j]);      // a power of two: exact
+    const float inv = 1.f / (*ascale * pow2_scale(__uint_as_float(colmax[j])));   // a power of two: exact
     u[e] = mk(re * inv, im * inv);
 }
 
@@ -482,11 +487,17 @@ void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64
         // FP16: column scales, B'^T, the product, the scaled reduction
         const __half* Ah = reinterpret_cast<const __half*>(Ap);
         const float* ascale = reinterpret_cast<const float*>(Ah + (size_t)nc * Kp);
-        float* bscale = P + (size_t)kMaxKSplit * nc * ldb;
+        unsigned int* colmax = reinterpret_cast<unsigned int*>(P + (size_t)kMaxKSplit * nc * ldb);
         __half* Bt = reinterpret_cast<__half*>(Bp);
         L.pre(KID_LAYOUT, 2.0 * nb + 16.0 * nc * s, 0);
-        k_colscale<<<s, 256, 0, L.st>>>(f, nc, s, bscale);
-        k_build_bt_h<<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, bscale, Bt, Kp, ldb);
+        cudaMemsetAsync(colmax, 0, sizeof(unsigned int) * s, L.st);
+        {
+            const int per = s < 256 ? 256 / s : 1;
+            long long want = ((long long)nc + per - 1) / per;
+            dim3 gcm((unsigned)(want < 2 * 152 ? want : 2 * 152), (unsigned)((s + 255) / 256));
+            k_colmax<<<gcm, 256, 0, L.st>>>(f, nc, s, colmax);
+        }
+        k_build_bt_h<<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, colmax, Bt, Kp, ldb);
         L.post();
         int kchunk = ((Kp / HBK + KS - 1) / KS) * HBK;
         dim3 grid((nc + HBM_ - 1) / HBM_, KS, ldb / HBN);
@@ -498,7 +509,7 @@ void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64
         L.post();
         L.pre(KID_LAYOUT, 4.0 * KS * nc * 2.0 * s + 8.0 * nc * s, 0);
         k_reduce_cprime_h<<<(unsigned)(((long long)nc * s + 255) / 256), 256, 0, L.st>>>(P, KS, nc, ldb, s,
-                                                                                          ascale, bscale, u);
+                                                                                          ascale, colmax, u);
         L.post();
         return;
     }
