@@ -38,11 +38,13 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, 152 SMs x ~2 FMA/clk x 2070 MHz
 # double-float peak in FP64-equivalent flops: 152 SMs x 128 FP32 lanes x 2.07 GHz
 # = 40.3 T instructions/s; one complex double-float MAC = 48 instructions = 8 flops
 DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
-# Measured DRAM bytes (read + write, ncu) over algorithmic bytes for a kernel
-# class, from six launches of one 5 Hz salt solve: reads match the
-# algorithmic count, about 40% of the written bytes are still in L2 when the
-# launch ends.  Valid while the kernel is unchanged.
-TRAFFIC_RATIO = {}
+# Measured DRAM bytes (read + write, ncu, every launch of one 5 Hz salt solve)
+# over the profiler's algorithmic bytes, per kernel class: the QR Grams are
+# self-products that read their block once (the algorithmic count reads it
+# twice); part of an update's written lines are still in L2 when it ends.
+# Valid while these kernels are unchanged.
+TRAFFIC_RATIO = {"gram_dd": (0.744, "profiles/traffic_salt2d_512x256_5hz.md"),
+                 "combine_dd": (0.923, "profiles/traffic_salt2d_512x256_5hz.md")}
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
 SOLVER = dict(pre=2, post=2, jacobi_w=0.8)
