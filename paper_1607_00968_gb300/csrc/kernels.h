@@ -34,9 +34,13 @@ template <typename T, typename FT, typename Op>
 void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const cplx<T>* u,
                            const cplx<FT>* f, cplx<T>* rc, int s);
 
-// out[j] = sum_node conj(a) b per column (double accumulation; s <= 256)
+// out[j] = sum_node conj(a) b per column (double accumulation; s <= 256),
+// deterministic: per-CTA sums in part (kColdotBlocks x s) added in block
+// order by the last CTA, which resets *count (zero before the first call)
+constexpr int kColdotBlocks = 2 * 152;
 template <typename T>
-void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long long N, int s, double2* out);
+void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long long N, int s, double2* out,
+                   double2* part, unsigned int* count);
 // y[:, j] += sign * (num_j / den_j.x) x[:, j]
 template <typename T>
 void launch_kc_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, const double2* num,

@@ -626,7 +626,8 @@ __global__ void k_axpy(cplx<T>* __restrict__ y, const cplx<T>* __restrict__ x, l
 // y[node][j] += sign * (num_j / den_j) x[node][j].
 template <typename T>
 __global__ void __launch_bounds__(256) k_coldot(const cplx<T>* __restrict__ a, const cplx<T>* __restrict__ b,
-                                                 long long N, int s, double2* __restrict__ out) {
+                                                 long long N, int s, double2* __restrict__ out,
+                                                 double2* __restrict__ part, unsigned int* __restrict__ count) {
     __shared__ double2 red[256];
     const int per = 256 / s;
     const int j = threadIdx.x % s, sub = threadIdx.x / s;
@@ -639,12 +640,30 @@ __global__ void __launch_bounds__(256) k_coldot(const cplx<T>* __restrict__ a, c
         }
     red[threadIdx.x] = make_double2(sub < per ? re : 0.0, sub < per ? im : 0.0);
     __syncthreads();
+    // per-CTA sums, then the last CTA to finish adds them in block order (the
+    // result does not depend on scheduling); it also resets the counter
+    __shared__ bool last;
     if (sub == 0) {
         double tr = 0.0, ti = 0.0;
         for (int k = 0; k < per; ++k) { tr += red[k * s + j].x; ti += red[k * s + j].y; }
-        atomicAdd(&out[j].x, tr);
-        atomicAdd(&out[j].y, ti);
+        part[(long long)blockIdx.x * s + j] = make_double2(tr, ti);
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int jj = threadIdx.x; jj < s; jj += blockDim.x) {
+        double tr = 0.0, ti = 0.0;
+        for (unsigned int bk = 0; bk < gridDim.x; ++bk) {
+            const double2 v = part[(long long)bk * s + jj];
+            tr += v.x;
+            ti += v.y;
+        }
+        out[jj] = make_double2(tr, ti);
+    }
+    if (threadIdx.x == 0) *count = 0u;
 }
 
 template <typename T>
@@ -758,11 +777,11 @@ void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const 
 
 template <typename T>
 void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long long N, int s,
-                   double2* out) {
-    cudaMemsetAsync(out, 0, sizeof(double2) * s, L.st);
+                   double2* out, double2* part, unsigned int* count) {
     L.pre(KID_LAYOUT, 2.0 * N * s * cb<T>(), 8.0 * N * s);
     long long want = (N + 255) / 256;
-    k_coldot<T><<<(unsigned)(want < 2 * 152 ? (want < 1 ? 1 : want) : 2 * 152), 256, 0, L.st>>>(a, b, N, s, out);
+    k_coldot<T><<<(unsigned)(want < kColdotBlocks ? (want < 1 ? 1 : want) : kColdotBlocks), 256, 0, L.st>>>(
+        a, b, N, s, out, part, count);
     L.post();
 }
 
@@ -895,7 +914,7 @@ void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count
                                         cplx<T>*, int);                                          \
     template void launch_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, long long);            \
     template void launch_coldot<T>(const Launch&, const cplx<T>*, const cplx<T>*, long long, int, \
-                                   double2*);                                                    \
+                                   double2*, double2*, unsigned int*);                           \
     template void launch_kc_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, const double2*,      \
                                     const double2*, double, long long, int);                    \
     template void launch_residual<T, GalOp<T>>(const Launch&, const GalOp<T>&, const cplx<T>*,   \

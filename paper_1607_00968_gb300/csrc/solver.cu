@@ -187,6 +187,9 @@ struct helm_ctx {
     // helm::FMT_DD (unevaluated float pairs) on the complex64 path when the
     // double-float kernels cover the block shape, else complex128
     int kfmt = 0;
+    // K-cycle: per-CTA partial column products and the completion counter
+    double2* kpart = nullptr;
+    unsigned int* kcount = nullptr;
 
     Launch L() { return Launch{st, &launches, prof}; }
     long long N() const { return lv[0].g.N; }
@@ -307,17 +310,17 @@ void kcycle_correction(helm_ctx* c, int k, const cplx<T>* r, cplx<T>* e, int s) 
     helm::GalOp<T> op = gal_op<T>(c, k);
     cycle<T, T>(c, k, r, z1, s);
     helm::launch_apply<T, T, T, helm::GalOp<T>>(c->L(), op, z1, w1, s);
-    helm::launch_coldot<T>(c->L(), w1, w1, lev.g.N, s, d11);
-    helm::launch_coldot<T>(c->L(), w1, r, lev.g.N, s, d1r);
+    helm::launch_coldot<T>(c->L(), w1, w1, lev.g.N, s, d11, c->kpart, c->kcount);
+    helm::launch_coldot<T>(c->L(), w1, r, lev.g.N, s, d1r, c->kpart, c->kcount);
     cudaMemcpyAsync(r2, r, sizeof(cplx<T>) * n, cudaMemcpyDeviceToDevice, c->st);
     helm::launch_kc_axpy<T>(c->L(), r2, w1, d1r, d11, -1.0, lev.g.N, s);
     cycle<T, T>(c, k, r2, z2, s);
     helm::launch_apply<T, T, T, helm::GalOp<T>>(c->L(), op, z2, w2, s);
-    helm::launch_coldot<T>(c->L(), w1, w2, lev.g.N, s, d12);
+    helm::launch_coldot<T>(c->L(), w1, w2, lev.g.N, s, d12, c->kpart, c->kcount);
     helm::launch_kc_axpy<T>(c->L(), w2, w1, d12, d11, -1.0, lev.g.N, s);
     helm::launch_kc_axpy<T>(c->L(), z2, z1, d12, d11, -1.0, lev.g.N, s);
-    helm::launch_coldot<T>(c->L(), w2, w2, lev.g.N, s, d22);
-    helm::launch_coldot<T>(c->L(), w2, r2, lev.g.N, s, d2r);
+    helm::launch_coldot<T>(c->L(), w2, w2, lev.g.N, s, d22, c->kpart, c->kcount);
+    helm::launch_coldot<T>(c->L(), w2, r2, lev.g.N, s, d2r, c->kpart, c->kcount);
     helm::launch_zero(c->L(), e, sizeof(cplx<T>) * n);
     helm::launch_kc_axpy<T>(c->L(), e, z1, d1r, d11, 1.0, lev.g.N, s);
     helm::launch_kc_axpy<T>(c->L(), e, z2, d2r, d22, 1.0, lev.g.N, s);
@@ -389,6 +392,10 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
 // ---------------------------------------------------------------------------
 
 void free_workspace(helm_ctx* c) {
+    dfree(c->kpart);
+    dfree(c->kcount);
+    c->kpart = nullptr;
+    c->kcount = nullptr;
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
     for (auto& l : c->lv) {
@@ -480,6 +487,11 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
         CUDA_TRY(c, dalloc(&c->lr_out, 4 * 16 * (size_t)N * s));
         CUDA_TRY(c, dalloc(&c->lr_z2, sizeof(c64) * (size_t)N * s));
         CUDA_TRY(c, dalloc(&c->lr_rho_new, sizeof(float) * s));
+    }
+    if (c->p.cycle_gamma == 3) {
+        CUDA_TRY(c, dalloc(&c->kpart, sizeof(double2) * helm::kColdotBlocks * (size_t)s));
+        CUDA_TRY(c, dalloc(&c->kcount, sizeof(unsigned int)));
+        CUDA_TRY(c, cudaMemsetAsync(c->kcount, 0, sizeof(unsigned int), c->st));
     }
     c->s_cap = s;
     return HELM_OK;
