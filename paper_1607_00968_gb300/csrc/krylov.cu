@@ -514,10 +514,22 @@ __global__ void __launch_bounds__(128) k_gram_sb4_hi(const char* __restrict__ X,
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.f;
-    for (long long n = n0 + r; active && n < n1; n += R) {
-        const float4 xv = *reinterpret_cast<const float4*>(Xh + n * s + g * 4 + 2 * h);
-        const float4 y0 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4);
-        const float4 y1 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4 + 2);
+    // the next node's operands are loaded while the current one is used
+    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f), y0 = xv, y1 = xv;
+    long long n = n0 + r;
+    if (active && n < n1) {
+        xv = *reinterpret_cast<const float4*>(Xh + n * s + g * 4 + 2 * h);
+        y0 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4);
+        y1 = *reinterpret_cast<const float4*>(Yh + n * s + g * 4 + 2);
+    }
+    for (; active && n < n1; n += R) {
+        const long long nn = n + R;
+        float4 xn = xv, y0n = y0, y1n = y1;
+        if (nn < n1) {
+            xn = *reinterpret_cast<const float4*>(Xh + nn * s + g * 4 + 2 * h);
+            y0n = *reinterpret_cast<const float4*>(Yh + nn * s + g * 4);
+            y1n = *reinterpret_cast<const float4*>(Yh + nn * s + g * 4 + 2);
+        }
         const float xr[2] = {xv.x, xv.z}, xi[2] = {xv.y, xv.w};
         const float yr[4] = {y0.x, y0.z, y1.x, y1.z}, yi[4] = {y0.y, y0.w, y1.y, y1.w};
 #pragma unroll
@@ -528,6 +540,9 @@ __global__ void __launch_bounds__(128) k_gram_sb4_hi(const char* __restrict__ X,
                 acc[a][b][0] = fmaf(xr[a], yr[b], fmaf(xi[a], yi[b], acc[a][b][0]));
                 acc[a][b][1] = fmaf(xr[a], yi[b], fmaf(-xi[a], yr[b], acc[a][b][1]));
             }
+        xv = xn;
+        y0 = y0n;
+        y1 = y1n;
     }
     const int E1 = G * 16;
     if (active)
@@ -671,9 +686,23 @@ __global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, 
         const int g = (int)(t - node * G);
         const long long e0 = node * s + g * 4;
         float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+        // the base pairs and the first block are requested up front, the next
+        // block while the current one is used
+        float2* o = reinterpret_cast<float2*>(out);
+        const float2* bs = reinterpret_cast<const float2*>(base);
+        const float4 oh0 = reinterpret_cast<const float4*>(bs + e0)[0], oh1 = reinterpret_cast<const float4*>(bs + e0)[1];
+        const float4 ol0 = reinterpret_cast<const float4*>(bs + plane + e0)[0],
+                     ol1 = reinterpret_cast<const float4*>(bs + plane + e0)[1];
+        const float4* xp0 = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(X) + e0);
+        float4 x01 = xp0[0], x23 = xp0[1];
         for (int i = 0; i < nb; ++i) {
-            const float4* xp = reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(X + (long long)i * xstride) + e0);
-            const float4 x01 = xp[0], x23 = xp[1];
+            float4 n01 = x01, n23 = x23;
+            if (i + 1 < nb) {
+                const float4* xq = reinterpret_cast<const float4*>(
+                    reinterpret_cast<const float2*>(X + (long long)(i + 1) * xstride) + e0);
+                n01 = xq[0];
+                n23 = xq[1];
+            }
             const float xr[4] = {x01.x, x01.z, x23.x, x23.z}, xi[4] = {x01.y, x01.w, x23.y, x23.w};
             const float2* ci = cs2 + (long long)i * 16 * G + g;
 #pragma unroll
@@ -684,12 +713,9 @@ __global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, 
                     ar[b] = fmaf(xr[a], c.x, fmaf(-xi[a], c.y, ar[b]));
                     ai[b] = fmaf(xr[a], c.y, fmaf(xi[a], c.x, ai[b]));
                 }
+            x01 = n01;
+            x23 = n23;
         }
-        float2* o = reinterpret_cast<float2*>(out);
-        const float2* bs = reinterpret_cast<const float2*>(base);
-        const float4 oh0 = reinterpret_cast<const float4*>(bs + e0)[0], oh1 = reinterpret_cast<const float4*>(bs + e0)[1];
-        const float4 ol0 = reinterpret_cast<const float4*>(bs + plane + e0)[0],
-                     ol1 = reinterpret_cast<const float4*>(bs + plane + e0)[1];
         const float ohv[8] = {oh0.x, oh0.y, oh0.z, oh0.w, oh1.x, oh1.y, oh1.z, oh1.w};
         const float olv[8] = {ol0.x, ol0.y, ol0.z, ol0.w, ol1.x, ol1.y, ol1.z, ol1.w};
         float hv[8], lv[8];
