@@ -488,6 +488,72 @@ __global__ void __launch_bounds__(128) k_gram_sb4(const char* __restrict__ X, lo
     }
 }
 
+// Self-Gram W^H W of groups of four (the block QR's Grams): Hermitian, so
+// only the 10 entries a <= b of each 4 x 4 group are formed, 5 per thread:
+// h = 0 takes (0,0) (0,1) (0,2) (0,3) (1,1), h = 1 takes (1,2) (1,3) (2,2)
+// (2,3) (3,3); the entries below the diagonal are written as conjugates.
+template <int F>
+__global__ void __launch_bounds__(128) k_gram_sb4_self(const char* __restrict__ X, long long N, int s,
+                                                        int chunks, c128* __restrict__ partial) {
+    extern __shared__ double2 red4[];              // R x G x 16
+    const int G = s / 4;
+    const int T = 2 * G;
+    const int R = 128 / T;
+    const int q = threadIdx.x % T, r = threadIdx.x / T;
+    const int g = q >> 1, h = q & 1;
+    const bool active = r < R;
+    const int chunk = blockIdx.y;
+    const long long plane = N * s;
+    const long long per = (N + chunks - 1) / chunks;
+    const long long n0 = (long long)chunk * per;
+    const long long n1 = n0 + per < N ? n0 + per : N;
+    float S[5][2], Lc[5][2];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) S[k][0] = S[k][1] = Lc[k][0] = Lc[k][1] = 0.f;
+    float4 wc[4], wn[4];
+    long long n = n0 + r;
+    if (active && n < n1) ld4<F>(X, plane, n * s + g * 4, wc);
+    for (; active && n < n1; n += R) {
+        const long long nn = n + R;
+        if (nn < n1) ld4<F>(X, plane, nn * s + g * 4, wn);
+        // operands by selection (no register-array indexing by h):
+        // h = 0: x = w0 w0 w0 w0 w1, y = w0 w1 w2 w3 w1
+        // h = 1: x = w1 w1 w2 w2 w3, y = w2 w3 w2 w3 w3
+        const float4 xs[5] = {h ? wc[1] : wc[0], h ? wc[1] : wc[0], h ? wc[2] : wc[0], h ? wc[2] : wc[0],
+                              h ? wc[3] : wc[1]};
+        const float4 ys[5] = {h ? wc[2] : wc[0], h ? wc[3] : wc[1], h ? wc[2] : wc[2], h ? wc[3] : wc[3],
+                              h ? wc[3] : wc[1]};
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const float4 x = xs[k], y = ys[k];
+            dd_mac(S[k][0], Lc[k][0], x.x, x.y, y.x, y.y);
+            dd_mac(S[k][0], Lc[k][0], x.z, x.w, y.z, y.w);
+            dd_mac(S[k][1], Lc[k][1], x.x, x.y, y.z, y.w);
+            dd_mac(S[k][1], Lc[k][1], -x.z, -x.w, y.x, y.y);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) wc[a] = wn[a];
+    }
+    const int E1 = G * 16;
+    if (active)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int a = h ? (k < 2 ? 1 : (k < 4 ? 2 : 3)) : (k < 4 ? 0 : 1);
+            const int b = h ? (k == 0 || k == 2 ? 2 : 3) : (k < 4 ? k : 1);
+            const double re = f2d_bits(S[k][0]) + f2d_bits(Lc[k][0]);
+            const double im = f2d_bits(S[k][1]) + f2d_bits(Lc[k][1]);
+            red4[(long long)r * E1 + g * 16 + a * 4 + b] = make_double2(re, im);
+            if (a != b) red4[(long long)r * E1 + g * 16 + b * 4 + a] = make_double2(re, -im);
+        }
+    __syncthreads();
+    c128* out = partial + (long long)chunk * E1;
+    for (int e = threadIdx.x; e < E1; e += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < R; ++k) { re += red4[(long long)k * E1 + e].x; im += red4[(long long)k * E1 + e].y; }
+        out[e] = mk(re, im);
+    }
+}
+
 // First Gram-Schmidt pass of float-pair blocks: the same products from the
 // hi planes only, in FP32 (4 FMA per complex product; each thread sums its
 // nodes in FP32, replicas and chunks are added in FP64).  Its error, a few
@@ -987,11 +1053,32 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
     dim3 grid(chunks, nb);
     const bool dd = emulate && gram_dd_ok(s, sb);
     const bool hi = hi_only && dd && sb == 4 && s % 4 == 0 && s <= 256 && xf == FMT_DD && yf == FMT_DD;
+    const bool self4 = dd && !hi && sb == 4 && s % 4 == 0 && s <= 256 && nb == 1 && X == Y && xf == yf &&
+                       (xf == FMT_DD || xf == FMT_C128);
     if (hi)   // FP32 products of the hi planes: 8 bytes per element and block
         L.pre(KID_GRAM_HI, (nb + 1.0) * N * s * 8.0, 8.0 * nb * (double)N * s * sb);
+    else if (self4)   // Hermitian: one read of the block, 10 of 16 entries per group
+        L.pre(KID_GRAM_DD, N * s * 16.0, 8.0 * (double)N * s * sb * (10.0 / 16.0));
     else
         L.pre(dd ? KID_GRAM_DD : KID_GRAM, (nb + 1.0) * N * s * 16.0, 8.0 * nb * (double)N * s * sb);
-    if (dd && sb == 4 && s % 4 == 0 && s <= 256) {
+    if (self4) {
+        // Hermitian self-Gram: 10 of the 16 entries of each group
+        const int G4 = s / 4;
+        const int R4 = 128 / (2 * G4);
+        const size_t sm4 = (size_t)R4 * G4 * 16 * sizeof(double2);
+        auto go = [&](auto kern) {
+            if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+            long long tiles = (N + R4 - 1) / R4;
+            long long want = (long long)resident_ctas(kern, 128, sm4) * 152;
+            int ch = (int)(tiles < want ? tiles : want);
+            if (ch > chunks) ch = chunks;
+            if (ch < 1) ch = 1;
+            kern<<<dim3(1, ch), 128, sm4, L.st>>>(static_cast<const char*>(X), N, s, ch, partial);
+            chunks = ch;
+        };
+        if (xf == FMT_DD) go(k_gram_sb4_self<FMT_DD>);
+        else go(k_gram_sb4_self<FMT_C128>);
+    } else if (dd && sb == 4 && s % 4 == 0 && s <= 256) {
         // groups of four: 128-thread CTAs, about three per SM in one wave
         const int G4 = s / 4;
         const int R4 = 128 / (2 * G4);
