@@ -39,11 +39,10 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, 152 SMs x ~2 FMA/clk x 2070 MHz
 # = 40.3 T instructions/s; one complex double-float MAC = 48 instructions = 8 flops
 DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
 # Measured DRAM bytes (read + write, ncu, every launch of one 5 Hz salt solve)
-# over the profiler's algorithmic bytes, per kernel class: the QR Grams are
-# self-products that read their block once (the algorithmic count reads it
-# twice); part of an update's written lines are still in L2 when it ends.
-# Valid while these kernels are unchanged.
-TRAFFIC_RATIO = {"gram_dd": (0.744, "profiles/traffic_salt2d_512x256_5hz.md"),
+# over the profiler's algorithmic bytes, per kernel class (the Grams read
+# exactly their operands; part of an update's written lines are still in L2
+# when it ends).  Valid while these kernels are unchanged.
+TRAFFIC_RATIO = {"gram_dd": (1.001, "profiles/traffic_salt2d_512x256_5hz.md"),
                  "combine_dd": (0.923, "profiles/traffic_salt2d_512x256_5hz.md")}
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
