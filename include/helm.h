@@ -95,7 +95,9 @@ typedef struct {
                                     must outlive the context; required by
                                     HELM_MIXED_C64_LEARNED (2D only)            */
     int coarse_tf32x3;       /* complex64 coarsest solve on the tensor cores:
-                                0 = one tf32 product (~1e-3 relative),
+                                0 = one FP16 product (11 significant bits,
+                                power-of-two scales of the inverse and of
+                                each right-hand side; ~1e-3 relative),
                                 1 = three tf32 products on hi/lo splits
                                 (FP32-class)                                    */
     int cycle_gamma;         /* 1 = V-cycle, 2 = W-cycle (two coarse visits per
@@ -219,7 +221,8 @@ helm_status helm_prolong_add(helm_ctx* ctx, int level, int prec,
                              const void* ec, void* u, int s);
 
 /* u = M_L^{-1} f on the coarsest level (dense inverse times the block):
-   FP64 for prec 0, tensor-core tf32 (see coarse_tf32x3) for prec 1. */
+   FP64 for prec 0, tensor cores (FP16, or three tf32 products: see
+   coarse_tf32x3) for prec 1. */
 helm_status helm_coarse_solve(helm_ctx* ctx, int prec, const void* f, void* u,
                               int s);
 
