@@ -213,6 +213,20 @@ def cpu_model():
 # reference arm: the CPU oracle as it stands
 # --------------------------------------------------------------------------
 
+def salt_config(args, world):
+    """The workload description both arms print (the salt workload, our
+    solver settings)."""
+    nodes = 513 * 257
+    basis_gb = (args.restart + 1) * NSRC * nodes * 16 / 1e9
+    return {"workload": "salt2d_512x256_64src_5freq", "grid_cells": [512, 256],
+            "nodes": nodes, "sources": NSRC, "freqs_hz": list(FREQS_HZ),
+            "tol": TOL, "shift": args.shift, "restart": args.restart,
+            "block": args.block, "levels": args.levels, "smoother": "V(2,2) Jacobi 0.8",
+            "precision": "complex64 cycle, FP64 Krylov",
+            "l2": "no flush: the Krylov basis (%.1f GB) exceeds L2" % basis_gb,
+            "parallelism": "dp%d (independent models per rank)" % world}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -238,8 +252,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": "salt2d_512x256_64src_5freq", "sample": "4 sources at 2 Hz per step",
-                   "shift": args.shift, "restart": args.restart, "levels": args.levels},
+        "config": salt_config(args, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
                          "sample": "4 of 64 sources at 2 Hz per step, numpy/scipy FP64 oracle, "
                                    "set-up excluded; " + cpu_model()},
@@ -579,14 +592,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
             "data": "synthetic",
-            "config": {"workload": "salt2d_512x256_64src_5freq", "grid_cells": [512, 256],
-                       "nodes": 131841, "sources": NSRC, "freqs_hz": list(FREQS_HZ),
-                       "tol": TOL, "shift": args.shift, "restart": args.restart,
-                       "block": args.block, "levels": args.levels, "smoother": "V(2,2) Jacobi 0.8",
-                       "precision": "complex64 cycle, FP64 Krylov",
-                       "l2": "no flush: the Krylov basis (%.1f GB) exceeds L2" %
-                             ((args.restart + 1) * Q.nbytes / 1e9),
-                       "parallelism": "dp%d (independent models per rank)" % world},
+            "config": salt_config(args, world),
             "cycles_per_frequency": iters, "max_relres": relres,
             "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg, "eikonal": eik,
             "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
