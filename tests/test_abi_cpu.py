@@ -62,3 +62,42 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.helm_solve(None, None, 1, 1e-6, None, None) == HELM_ERR_ARG
     assert lib.helm_kernel_launches(None) == 0
     lib.helm_destroy(None)
+
+
+def test_setup_rejects_unsupported_method_combinations(lib):
+    from paper_1607_00968_gb300.helm import HelmParams, HELM_ERR_ARG
+    p = HelmParams()
+    lib.helm_default_params(ctypes.byref(p))
+    p.dim, p.h, p.omega = 2, 1.0, 1.0
+    p.n[0], p.n[1] = 32, 16
+    ctx = ctypes.c_void_p()
+    dummy = ctypes.c_void_p(16)
+    p.cycle_gamma, p.krylov = 3, 1          # the K-cycle is nonlinear: FGMRES only
+    assert lib.helm_setup(dummy, dummy, ctypes.byref(p), None, ctypes.byref(ctx)) == HELM_ERR_ARG
+    p.cycle_gamma, p.krylov = 4, 0
+    assert lib.helm_setup(dummy, dummy, ctypes.byref(p), None, ctypes.byref(ctx)) == HELM_ERR_ARG
+    p.cycle_gamma, p.krylov, p.prec, p.block = 2, 1, 1, 4   # complex64 BiCGSTAB needs block <= 2
+    assert lib.helm_setup(dummy, dummy, ctypes.byref(p), None, ctypes.byref(ctx)) == HELM_ERR_ARG
+    p.cycle_gamma, p.krylov, p.prec, p.block = 1, 0, 2, 4   # learned stage without weights
+    assert lib.helm_setup(dummy, dummy, ctypes.byref(p), None, ctypes.byref(ctx)) == HELM_ERR_ARG
+    assert not ctx.value
+
+
+def test_eikonal_and_profiler_argument_checks(lib):
+    from paper_1607_00968_gb300.helm import HELM_ERR_ARG
+    e = ctypes.c_void_p()
+    n = (ctypes.c_int * 3)(16, 8, 0)
+    assert lib.helm_eik_create(4, n, 10.0, 1, None, ctypes.byref(e)) == HELM_ERR_ARG
+    assert lib.helm_eik_create(2, None, 10.0, 1, None, ctypes.byref(e)) == HELM_ERR_ARG
+    assert lib.helm_eik_create(2, n, 0.0, 1, None, ctypes.byref(e)) == HELM_ERR_ARG
+    assert lib.helm_eik_create(2, n, 10.0, 0, None, ctypes.byref(e)) == HELM_ERR_ARG
+    bad = (ctypes.c_int * 3)(16, 0, 0)
+    assert lib.helm_eik_create(2, bad, 10.0, 1, None, ctypes.byref(e)) == HELM_ERR_ARG
+    assert not e.value
+    assert lib.helm_eik_forward(None, None, None, 1, None, None, None, None) == HELM_ERR_ARG
+    assert lib.helm_eik_jv(None, None, None) == HELM_ERR_ARG
+    assert lib.helm_eik_jtw(None, None, None) == HELM_ERR_ARG
+    assert lib.helm_eik_last_error(None) == b""
+    lib.helm_eik_destroy(None)
+    assert lib.helm_profile_enable(None, 1) == HELM_ERR_ARG
+    assert lib.helm_profile_select(None, 0) == HELM_ERR_ARG
