@@ -273,6 +273,128 @@ def test_two_grid_without_smoothing_is_coarse_projection():
     np.testing.assert_allclose(out, Pe, rtol=1e-9, atol=1e-12 * np.abs(Pe).max())
 
 
+def test_jacobi_sweeps_hand_computed():
+    """Damped Jacobi with weight 0.8 on a 3-node 1D operator, worked by hand.
+    h = 1, omega = 1, m = (1, 2, 1), gamma = 0, shift 0.5, so c = m (1 - 0.5i)
+    and M = tridiag(-1, 2, -1) - diag(c) has diagonal (1 + 0.5i, 1i, 1 + 0.5i).
+    From u = (1, 0, 0) with f = (0, 1, 0): r = (-1 - 0.5i, 2, 0), D^-1 r =
+    (-1, -2i, 0), so one sweep gives (0.2, -1.6i, 0); a second sweep gives
+    (-0.472 - 1.024i, -1.28i, -0.512 - 1.024i).  A wrong weight, a wrong sign
+    or a diagonal without the shift (diag(A)) changes these numbers."""
+    M = O.helmholtz_matrix(np.array([1.0, 2.0, 1.0]), np.zeros(3), 1.0, 1.0, 0.5)
+    np.testing.assert_allclose(M.diagonal(), [1 + 0.5j, 1j, 1 + 0.5j], rtol=0, atol=1e-15)
+    u0 = np.array([[1.0], [0.0], [0.0]], dtype=complex)
+    f = np.array([[0.0], [1.0], [0.0]], dtype=complex)
+    one = O.jacobi(M, M.diagonal(), u0, f, 0.8, 1).ravel()
+    two = O.jacobi(M, M.diagonal(), u0, f, 0.8, 2).ravel()
+    np.testing.assert_allclose(one, [0.2, -1.6j, 0.0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(two, [-0.472 - 1.024j, -1.28j, -0.512 - 1.024j], rtol=0, atol=1e-14)
+
+
+def test_jacobi_zero_guess_sweep_is_scaled_diagonal_solve():
+    """One sweep from u = 0 is 0.8 f / diag(M), elementwise."""
+    p = small_problem()
+    M = O.helmholtz_matrix(p["m"], p["gamma"], p["omega"], p["h"], 0.5)
+    rng = np.random.default_rng(21)
+    f = crand(rng, M.shape[0], 3)
+    u = O.jacobi(M, M.diagonal(), np.zeros_like(f), f, 0.8, 1)
+    np.testing.assert_allclose(u, 0.8 * f / M.diagonal()[:, None], rtol=1e-15)
+
+
+def _interp_1d(nc):
+    """Linear interpolation written out from its definition: coarse node J
+    sits on fine node 2J (weight 1) and feeds its two fine neighbours 2J - 1,
+    2J + 1 with weight 1/2."""
+    nf = 2 * nc - 1
+    P = np.zeros((nf, nc))
+    for J in range(nc):
+        P[2 * J, J] = 1.0
+        if 2 * J - 1 >= 0:
+            P[2 * J - 1, J] = 0.5
+        if 2 * J + 1 < nf:
+            P[2 * J + 1, J] = 0.5
+    return P
+
+
+def _dense_cycle_operator(Md, shape, levels, pre, post, w, gamma):
+    """B with z = B f for the cycle of Alg. "Two-grid cycle" applied
+    recursively, from dense matrices only.  Its error propagation is
+        I - B M = S^post (I - P B_c^(gamma) P^T M) S^pre,
+    S = I - w D^-1 M with D = diag(M) of the shifted operator, M_c = P^T M P,
+    B_c^(gamma) = (I - (I - B_c M_c)^gamma) M_c^-1 (gamma cycles on the
+    coarse level, each on the residual of the last; the coarsest level is
+    solved exactly)."""
+    n = Md.shape[0]
+    if levels == 1:
+        return np.linalg.inv(Md)
+    P = _interp_1d((shape[0] - 1) // 2 + 1)
+    for ax in range(1, len(shape)):
+        P = np.kron(P, _interp_1d((shape[ax] - 1) // 2 + 1))
+    cshape = tuple((k - 1) // 2 + 1 for k in shape)
+    Mc = P.T @ Md @ P
+    Bc = _dense_cycle_operator(Mc, cshape, levels - 1, pre, post, w, gamma)
+    if levels - 1 > 1 and gamma == 2:
+        Ec = np.eye(Mc.shape[0]) - Bc @ Mc
+        Bc = (np.eye(Mc.shape[0]) - Ec @ Ec) @ np.linalg.inv(Mc)
+    I_ = np.eye(n)
+    S = I_ - w * np.diag(1.0 / np.diag(Md)) @ Md
+    E = np.linalg.matrix_power(S, post) @ (I_ - P @ Bc @ P.T @ Md) @ np.linalg.matrix_power(S, pre)
+    return (I_ - E) @ np.linalg.inv(Md)
+
+
+@pytest.mark.parametrize("levels,pre,post,gamma", [(2, 2, 2, 1), (2, 1, 0, 1), (2, 0, 1, 1),
+                                                   (2, 2, 1, 1), (3, 2, 2, 1), (3, 1, 2, 1),
+                                                   (3, 2, 2, 2)])
+def test_cycle_error_propagation_matches_dense_restatement(levels, pre, post, gamma):
+    """The oracle's cycle, applied to the columns of M (so that its output is
+    B M), against the dense error-propagation product of Alg. "Two-grid
+    cycle" on 9 x 5 nodes (weight 0.8 and D = diag(M) of the shifted operator,
+    written in the restatement).  Swapped pre/post counts, a missing sweep, a
+    sweep on the wrong level, another weight or diag(A) for diag(M) each
+    change B M."""
+    cells = (8, 4)
+    shape = I.node_shape(cells)
+    rng = np.random.default_rng(22)
+    m = rng.uniform(0.5, 1.5, shape)
+    gam = np.zeros(shape)
+    gam[:, :2] = 0.6
+    omega, h = 1.1, 1.0
+    M = O.helmholtz_matrix(m, gam, omega, h, 0.5)
+    Md = M.toarray()
+    H = O.Hierarchy(M, shape, levels)
+    if (pre, post, gamma) == (2, 2, 1):
+        got = O.vcycle(H, Md.astype(complex))           # defaults: V(2,2), weight 0.8
+    else:
+        got = O.vcycle(H, Md.astype(complex), 0, pre, post, 0.8, gamma)
+    want = _dense_cycle_operator(Md, shape, levels, pre, post, 0.8, gamma) @ Md
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_cycle_restatement_detects_planted_mistakes():
+    """The dense restatement separates the readings a mistake would give:
+    swapped pre/post counts, weight 1.0 for 0.8 and diag(A) for diag(M) all
+    move B M by far more than the tolerance of the test above."""
+    cells = (8, 4)
+    shape = I.node_shape(cells)
+    rng = np.random.default_rng(22)
+    m = rng.uniform(0.5, 1.5, shape)
+    gam = np.zeros(shape)
+    gam[:, :2] = 0.6
+    M = O.helmholtz_matrix(m, gam, 1.1, 1.0, 0.5).toarray()
+    A = O.helmholtz_matrix(m, gam, 1.1, 1.0, 0.0).toarray()
+    ref = _dense_cycle_operator(M, shape, 2, 2, 1, 0.8, 1) @ M
+    tol = 1e-11 * np.abs(ref).max()
+    assert np.abs(_dense_cycle_operator(M, shape, 2, 1, 2, 0.8, 1) @ M - ref).max() > 1e3 * tol
+    assert np.abs(_dense_cycle_operator(M, shape, 2, 2, 1, 1.0, 1) @ M - ref).max() > 1e3 * tol
+    # diag(A) in the smoother: restate S with the unshifted diagonal
+    n = M.shape[0]
+    P = np.kron(_interp_1d(3), _interp_1d(5))
+    Bc = np.linalg.inv(P.T @ M @ P)
+    S = np.eye(n) - 0.8 * np.diag(1.0 / np.diag(A)) @ M
+    E = S @ (np.eye(n) - P @ Bc @ P.T @ M) @ S @ S
+    assert np.abs((np.eye(n) - E) - ref).max() > 1e3 * tol
+
+
 def test_vcycle_is_linear():
     p = small_problem((16, 16))
     shape = p["m"].shape
