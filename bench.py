@@ -6,7 +6,7 @@ row, solved at the five frequencies 2, 3.5, 5, 6.5 and 8 Hz (one set-up per
 frequency, done before timing as in the paper's t_sol convention, Sec. 5.3
 table) -> 320 right-hand-side solves per step, each to true FP64 relative
 residual <= 1e-6.  Headline: the mixed-precision solver (complex64 multigrid
-cycle, FP64 Krylov); the plain complex128 solver is timed beside it.
+cycle, FP64-class double-float Krylov); the plain complex128 solver is timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank solves its own seeded model (weak scaling, no
@@ -35,9 +35,13 @@ TOL = 1e-6
 METRIC = "Helmholtz RHS-solves/s to rel-res 1e-6 (salt 512x256, 64 sources x 5 frequencies)"
 UNIT = "RHS-solves/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal, 152 SMs x ~2 FMA/clk x 2070 MHz x 2)
-# double-float peak in FP64-equivalent flops: 152 SMs x 128 FP32 lanes x 2.07 GHz
-# = 40.3 T instructions/s; one complex double-float MAC = 48 instructions = 8 flops
-DD_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 48 * 8 / 1e12
+
+
+def dd_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """Double-float peak in FP64-equivalent flops: SMs x 128 FP32 lanes x
+    clock = FP32 instructions/s; one complex double-float MAC = 48
+    instructions = 8 FP64 flops."""
+    return sms * 128 * sm_mhz * 1e6 / 48 * 8 / 1e12
 # Measured DRAM bytes (read + write, ncu, every launch of one 5 Hz salt solve)
 # over the profiler's algorithmic bytes, per kernel class (the Grams read
 # exactly their operands; part of an update's written lines are still in L2
@@ -162,7 +166,7 @@ def _oracle_worker(args, q):
         from paper_1607_00968_gb300 import inputs
         P = inputs.salt2d_problem(seed=args["seed"], freq_hz=args["freq"])
         S = O.Solver(P.m, P.gamma, P.omega, P.h, levels=args["levels"], shift=args["shift"])
-        cols = list(range(0, NSRC, NSRC // args["nrhs"]))[:args["nrhs"]]
+        cols = oracle_cols(args["nrhs"])
         Q = P.rhs(cols).T.copy()
         t0 = time.perf_counter()
         res = []
@@ -171,21 +175,35 @@ def _oracle_worker(args, q):
                                max_restarts=args["max_restarts"])
             res.append(float(O.relres(S.A, U, Q).max()))
         dt = time.perf_counter() - t0
-        q.put({"seconds": dt, "rhs": len(cols) * args["reps"], "relres": max(res),
-               "iters": [i.iters for i in infos], "converged": all(i.converged for i in infos)})
+        out = {"seconds": dt, "rhs": len(cols) * args["reps"], "relres": max(res),
+               "iters": [i.iters for i in infos], "converged": all(i.converged for i in infos)}
+        if args.get("gpu_u"):
+            # untimed: the GPU's solution of the same columns against the
+            # oracle's FP64 operator and its solve to 1e-10
+            Ug = np.load(args["gpu_u"])                       # (nrhs, N)
+            out["gpu_relres_by_oracle"] = float(O.relres(S.A, Ug.T, Q).max())
+            Ut, _ = S.solve(Q, tol=1e-10, restart=args["restart"], block=args["block"],
+                            max_restarts=200)
+            out["gpu_error_vs_oracle"] = float(max(np.linalg.norm(Ug[k] - Ut[:, k]) /
+                                                   np.linalg.norm(Ut[:, k]) for k in range(len(cols))))
+        q.put(out)
     except Exception as e:  # reported, never silently dropped
         q.put({"error": repr(e)})
 
 
+def oracle_cols(nrhs):
+    return list(range(0, NSRC, NSRC // nrhs))[:nrhs]
+
+
 def oracle_run(seed, freq, nrhs, shift, restart, block, levels, reps=1, max_restarts=50,
-               timeout=900):
+               timeout=900, gpu_u=None):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     threads = os.cpu_count() or 1
     p = ctx.Process(target=_oracle_worker, args=(dict(seed=seed, freq=freq, nrhs=nrhs, shift=shift,
                                                       restart=restart, block=block, reps=reps,
                                                       levels=levels,
-                                                      threads=threads,
+                                                      threads=threads, gpu_u=gpu_u,
                                                       max_restarts=max_restarts), q))
     p.start()
     try:
@@ -222,7 +240,11 @@ def salt_config(args, world):
             "nodes": nodes, "sources": NSRC, "freqs_hz": list(FREQS_HZ),
             "tol": TOL, "shift": args.shift, "restart": args.restart,
             "block": args.block, "levels": args.levels, "smoother": "V(2,2) Jacobi 0.8",
-            "precision": "complex64 cycle, FP64 Krylov",
+            "precision": "complex64 cycle (FP32 accumulation, FP16 coarsest product); "
+                         "double-float Krylov (float pairs, ~2^-46 per term: A Z, Gram, updates, "
+                         "QR); FP64 true residual and least squares",
+            "orthogonalisation": "one Gram-Schmidt + one Cholesky QR pass, each repeated when "
+                                 "its rounding test asks (orthogonality 1e-11)",
             "l2": "no flush: the Krylov basis (%.1f GB) exceeds L2" % basis_gb,
             "parallelism": "dp%d (independent models per rank)" % world}
 
@@ -336,12 +358,12 @@ def run_other(args):
             P = inputs.layered2d_problem(seed=args.seed)
             kw = dict(levels=3, restart=10, block=8, shift=0.5)
             runs = [("c128", "complex128, shift 0.5, 3 levels, V(2,2), FGMRES(10), block 8"),
-                    ("c64", "complex64 cycle + FP64 Krylov")]
+                    ("c64", "complex64 cycle + FP64-class (double-float) Krylov")]
             desc = "layered2d_128x64_8src_6Hz"
         else:
             P = inputs.layered3d_problem(seed=args.seed)
             kw = dict(levels=4, restart=5, block=32, shift=0.5)
-            runs = [("c64", "complex64 cycle + FP64 Krylov, shift 0.5, 4 levels, FGMRES(5), "
+            runs = [("c64", "complex64 cycle + FP64-class Krylov, shift 0.5, 4 levels, FGMRES(5), "
                             "block 32 (8 groups in lock step)")]
             desc = "layered3d_128x128x64_256src_4Hz"
         Q = torch.as_tensor(P.rhs()).cuda()
@@ -365,7 +387,7 @@ def run_other(args):
         head = runs[-1][0]
         line.update({"metric": "Helmholtz RHS-solves/s to rel-res 1e-6 (%s)" % desc,
                      "value": round(res[head]["value"], 3), "ms_per_step": res[head]["ms_per_step"],
-                     "dtype": "c64+f64" if head == "c64" else "c128",
+                     "dtype": "c64+dd" if head == "c64" else "c128",
                      "config": dict(workload=desc, nodes=P.n_nodes, sources=Q.shape[0],
                                     omega=P.omega, **kw), "runs": res})
     else:
@@ -481,12 +503,21 @@ def main():
                           device="cuda")
     iters = [int(np.max(i.iters)) for i in infos]
     relres = float(max(np.max(i.relres) for i in infos))
+    converged = all(bool(np.all(i.relres <= TOL)) and bool(np.all(i.status == 0)) for i in infos)
 
     # roofline of the dominant class from its events over the timed region
     d = merged_profile()[dom]
     for S in mixed:
         S.profile(False)
+    orth = {}
+    for S in mixed:
+        for k, v in S.orth_stats().items():
+            orth[k] = orth.get(k, 0) + v
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    props = torch.cuda.get_device_properties(local)
+    sms = int(props.multi_processor_count)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    dd_peak = dd_peak_tflops(sms, sm_mhz)
     kernels = {}
     for k, v in prof.items():                  # the profiled untimed step
         if v["launches"] == 0 or v["time_ms"] <= 0:
@@ -499,17 +530,21 @@ def main():
     dd_kernels = ("gram_dd", "combine_dd")
     if dom in fp64_kernels or dom in dd_kernels:
         achieved = d["flops"] / (d["time_ms"] / 1e3) / 1e12
-        peak = DD_PEAK_TFLOPS if dom in dd_kernels else FP64_PEAK_TFLOPS
+        peak = dd_peak if dom in dd_kernels else FP64_PEAK_TFLOPS
         roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 4),
                 "peak": round(peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": ("double-float on the FP32 pipes, FP64-equivalent (derived)"
+                "peak_source": ("double-float on the FP32 pipes, FP64-equivalent, derived: "
+                                "%d SMs (device query) x 128 FP32 lanes x %.0f MHz (sm_max_mhz of "
+                                "%s) / 48 instructions per complex MAC x 8 flops"
+                                % (sms, sm_mhz, peak_src)
                                 if dom in dd_kernels else "FP64 nominal (derived)")}
     else:
         achieved = d["bytes"] / (d["time_ms"] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                 "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
                 "peak_source": "hbm_gbs of %s" % peak_src}
+    roof["sm_count"] = sms
     roof["share_of_step"] = round(d["time_ms"] / ms, 4) if ms > 0 else None
     roof["launches"] = d["launches"]
     if dom in TRAFFIC_RATIO and d["launches"]:
@@ -534,6 +569,12 @@ def main():
     e2e = {"value": NSRC * len(FREQS_HZ) * args.steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(Q.nbytes * len(FREQS_HZ)),
            "d2h_bytes_per_step": int(Q.nbytes * len(FREQS_HZ))}
+    # the 2 Hz solution of the columns the CPU leg solves, for its error check
+    gpu_u = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        U2, _, _ = mixed[0].solve(Qd, TOL)
+        gpu_u = os.path.join(tempfile.mkdtemp(), "u2hz.npy")
+        np.save(gpu_u, U2[oracle_cols(4)].cpu().numpy())
     for S in mixed:
         S.close()
     del mixed
@@ -546,7 +587,9 @@ def main():
             S.solve(Qd, TOL)
         pms, pinfos = timed_steps(torch, ps, Qd, 1, stream)
         plain = {"value": NSRC * len(FREQS_HZ) / (pms / 1e3), "unit": UNIT, "ms_per_step": pms,
-                 "cycles": [int(np.max(i.iters)) for i in pinfos]}
+                 "cycles": [int(np.max(i.iters)) for i in pinfos],
+                 "max_relres": float(max(np.max(i.relres) for i in pinfos)),
+                 "converged": all(bool(np.all(i.relres <= TOL)) for i in pinfos)}
         for S in ps:
             S.close()
 
@@ -573,9 +616,10 @@ def main():
 
     # ---------------- CPU oracle baseline (rank 0, N = 1) ----------------
     cpu = None
+    oracle_check = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r = oracle_run(args.seed, FREQS_HZ[0], 4, args.shift, args.restart, min(args.block, 4),
-                       args.levels)
+                       args.levels, gpu_u=gpu_u)
         if "error" in r:
             cpu = {"value": None, "unit": UNIT, "cores": r.get("threads"), "kind": "oracle",
                    "sample": "failed: " + r["error"]}
@@ -585,17 +629,24 @@ def main():
                    "sample": "4 of 64 sources at 2 Hz solved to 1e-6 by the numpy/scipy FP64 "
                              "oracle (%.1f s, cycles %s), set-up excluded; %s"
                              % (r["seconds"], r["iters"], cpu_model())}
+            if "gpu_error_vs_oracle" in r:
+                oracle_check = {"columns": oracle_cols(4), "freq_hz": FREQS_HZ[0],
+                                "max_relres_by_oracle_operator": r["gpu_relres_by_oracle"],
+                                "max_error_vs_oracle_tol_1e-10": r["gpu_error_vs_oracle"]}
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": round(value, 3) if converged else None, "unit": UNIT,
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+dd",
             "data": "synthetic",
             "config": salt_config(args, world),
-            "cycles_per_frequency": iters, "max_relres": relres,
+            "status": "ok" if converged else "not converged: a column ended above tol (value withheld)",
+            "cycles_per_frequency": iters, "max_relres": relres, "orth": orth,
+            "oracle_check": oracle_check,
             "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg, "eikonal": eik,
-            "speedup_vs_plain": round(value / plain["value"], 3) if plain else None,
+            "speedup_vs_plain": round(value / plain["value"], 3) if (plain and converged) else None,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,
         }

@@ -123,6 +123,21 @@ typedef struct {
                                 (launch-bound sizes).  Never while the
                                 profiler is on (it times single launches).
                                 Results are identical either way.            */
+    int orth;                /* block FGMRES orthogonalisation of each new
+                                block W = A Z_j against the basis and its own
+                                QR (Sec. 5.3 block FGMRES; the paper leaves
+                                the scheme open):
+                                0 = one classical Gram-Schmidt pass and one
+                                Cholesky QR pass, each repeated only when its
+                                rounding could leave the new basis block less
+                                orthogonal than 1e-11 (second Gram-Schmidt
+                                pass when u / sin(theta_min) * kappa_F(W')
+                                > 1e-11, second Cholesky QR pass when
+                                u * kappa_F(W')^2 > 1e-11, u = 2^-53 in FP64
+                                and 2^-46 for the float-pair arithmetic of
+                                the complex64 path);
+                                1 = always two passes of each (CGS2 +
+                                CholQR2)                                      */
 } helm_params;
 
 typedef struct {
@@ -135,7 +150,7 @@ typedef struct {
 
 /* Fill p with the defaults of Sec. 5.3 (levels 3, V(2,2), weight 0.8,
    restart 10) plus shift 0.5, block 8, max_restarts 50, HELM_PLAIN_C128,
-   coarse_tf32x3 0, cycle_gamma 1, krylov 0, graphs 2. */
+   coarse_tf32x3 0, cycle_gamma 1, krylov 0, graphs 2, orth 0. */
 void helm_default_params(helm_params* p);
 
 /* Set up the hierarchy for one (m, gamma, omega) (Sec. 4: set-up once, reused
@@ -231,10 +246,11 @@ helm_status helm_coarse_solve(helm_ctx* ctx, int prec, const void* f, void* u,
 helm_status helm_vcycle(helm_ctx* ctx, int prec, const void* f, void* z, int s);
 
 /* helm_vcycle without any allocation.  It exists for callers that cannot
-   call cudaMalloc at solve time: code running while a CUDA stream is being
-   captured into a graph, latency-bound loops that cannot afford the device
-   synchronisation an allocation may cause, or frameworks whose allocator
-   owns all device memory.  It computes what helm_vcycle computes (same
+   call cudaMalloc at solve time: latency-bound loops that cannot afford the
+   device synchronisation an allocation may cause, or frameworks whose
+   allocator owns all device memory and forbid others to take more.  Like
+   every call here it returns after synchronising the context's stream.
+   It computes what helm_vcycle computes (same
    kernels, same arguments and layouts), but its level buffers live in one
    fixed 64 MiB device array compiled into libhelm instead of context
    workspace; every GPU that loads libhelm holds that array until the process
@@ -262,6 +278,13 @@ helm_status helm_get_operator(const helm_ctx* ctx, int level, void* coef_host);
 
 /* Number of kernels libhelm launched on this context since set-up. */
 long long helm_kernel_launches(const helm_ctx* ctx);
+
+/* Orthogonalisation counters of block FGMRES since set-up (see the orth
+   field of helm_params): qr = block QR factorisations (one per Krylov step
+   and one per restart), reorth = steps whose Gram-Schmidt pass was repeated,
+   qr2 = QRs that took a second Cholesky pass.  Any pointer may be NULL.
+   HELM_ERR_ARG if ctx is NULL. */
+helm_status helm_orth_stats(const helm_ctx* ctx, long long* qr, long long* reorth, long long* qr2);
 
 /* ---------------------------------------------------------------------
  * Learned preconditioning stage (not in the paper; it relies on FGMRES

@@ -301,6 +301,20 @@ struct Profiler;  // host side, defined in solver.cu
 void prof_begin(Profiler* p, cudaStream_t st, int kid, double bytes, double flops);
 void prof_end(Profiler* p, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount),
+// read once per device; launch shapes are sized in multiples of it.
+inline int sm_count() {
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 struct Launch {
     cudaStream_t st;
     long long* counter;  // incremented once per kernel launch

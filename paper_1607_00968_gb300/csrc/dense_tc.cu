@@ -14,7 +14,7 @@
 // accumulation, fed by a 4-stage cp.async pipeline, and the reduction of the
 // K slices removes the scales exactly.  The FP32-class option keeps A' in
 // FP32 and runs three mma.sync m16n8k8 tf32 products on hi/lo splits.  The K
-// range is split over CTAs so that the ~nc/128 row tiles fill the 152 SMs.
+// range is split over CTAs so that the ~nc/128 row tiles fill the SMs.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -440,7 +440,7 @@ constexpr int kMaxKSplit = 16;
 int dense_tc_ksplit(int nc, int s) {
     const int mt = (nc + TBM - 1) / TBM, nt = dense_tc_ldb(s) / TBN;
     const int kt = dense_tc_kpad(nc) / TBK;
-    const long long slots = 2LL * 152;
+    const long long slots = 2LL * sm_count();
     int best = 1;
     double best_cost = 1e300;
     for (int ks = 1; ks <= kMaxKSplit; ++ks) {
@@ -494,7 +494,8 @@ void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64
         {
             const int per = s < 256 ? 256 / s : 1;
             long long want = ((long long)nc + per - 1) / per;
-            dim3 gcm((unsigned)(want < 2 * 152 ? want : 2 * 152), (unsigned)((s + 255) / 256));
+            const long long cap = 2LL * sm_count();
+            dim3 gcm((unsigned)(want < cap ? want : cap), (unsigned)((s + 255) / 256));
             k_colmax<<<gcm, 256, 0, L.st>>>(f, nc, s, colmax);
         }
         k_build_bt_h<<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, colmax, Bt, Kp, ldb);

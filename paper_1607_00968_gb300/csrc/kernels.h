@@ -36,8 +36,9 @@ void launch_resid_restrict(const Launch& L, const Op& op, const Grid& gc, const 
 
 // out[j] = sum_node conj(a) b per column (double accumulation; s <= 256),
 // deterministic: per-CTA sums in part (kColdotBlocks x s) added in block
-// order by the last CTA, which resets *count (zero before the first call)
-constexpr int kColdotBlocks = 2 * 152;
+// order by the last CTA, which resets *count (zero before the first call);
+// at most kColdotBlocks CTAs (two per SM), the size of `part`
+constexpr int kColdotBlocks = 1024;
 template <typename T>
 void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long long N, int s, double2* out,
                    double2* part, unsigned int* count);

@@ -14,7 +14,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kGramEPT = 8;          // accumulators per thread in the Gram kernel
 constexpr int kGramTileElems = 1024; // node-tile size (nodes x s) staged in shared memory
-constexpr int kTargetCTAs = 4 * 152; // 4 waves' worth of CTAs on 152 SMs
 
 inline int blocks_for(long long total) {
     long long b = (total + kThreads - 1) / kThreads;
@@ -28,7 +27,7 @@ __host__ __device__ inline int gram_tile_nodes(int s) { return s >= kGramTileEle
 inline int gram_chunks(long long N, int nb, int s) {
     long long tn = gram_tile_nodes(s);
     long long tiles = (N + tn - 1) / tn;
-    long long want = (kTargetCTAs + nb - 1) / nb;
+    long long want = (4LL * sm_count() + nb - 1) / nb;   // 4 waves' worth of CTAs
     if (want < 1) want = 1;
     return (int)(tiles < want ? tiles : want);
 }
@@ -1069,7 +1068,7 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
         auto go = [&](auto kern) {
             if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
             long long tiles = (N + R4 - 1) / R4;
-            long long want = (long long)resident_ctas(kern, 128, sm4) * 152;
+            long long want = (long long)resident_ctas(kern, 128, sm4) * sm_count();
             int ch = (int)(tiles < want ? tiles : want);
             if (ch > chunks) ch = chunks;
             if (ch < 1) ch = 1;
@@ -1090,7 +1089,7 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
             if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
             // one wave of resident CTAs over the nb blocks
             long long tiles = (N + R4 - 1) / R4;
-            long long want = ((long long)resident_ctas(kern, 128, sm4) * 152 + nb - 1) / nb;
+            long long want = ((long long)resident_ctas(kern, 128, sm4) * sm_count() + nb - 1) / nb;
             int ch = (int)(tiles < want ? tiles : want);
             if (ch > chunks) ch = chunks;          // the partial buffer holds gram_chunks() slots
             if (ch < 1) ch = 1;
@@ -1157,7 +1156,8 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
         const int G = (s + sb - 1) / sb;
         size_t smem = (size_t)(T * s + G * sb * sb) * sizeof(float4);
         long long ntiles = (N + T - 1) / T;
-        int grid = (int)(ntiles < 4LL * 152 * 4 ? ntiles : 4LL * 152 * 4);
+        const long long gcap = 16LL * sm_count();
+        int grid = (int)(ntiles < gcap ? ntiles : gcap);
         long long nc = (long long)nb * G * sb * sb;
         L.pre(KID_LAYOUT, 32.0 * nc, 0);
         k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
@@ -1170,7 +1170,7 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
             if (sm2 > 48 * 1024)
                 cudaFuncSetAttribute(k_combine_sb4_hi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
             long long want = (total + 255) / 256;
-            long long cap = (long long)resident_ctas(k_combine_sb4_hi, 256, sm2) * 152;
+            long long cap = (long long)resident_ctas(k_combine_sb4_hi, 256, sm2) * sm_count();
             const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
             k_combine_sb4_hi<<<g4, 256, sm2, L.st>>>(static_cast<char*>(out),
                                                      static_cast<const char*>(base ? base : out), sign,
@@ -1189,7 +1189,7 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
                 if (sm4 > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
                 // one wave of resident CTAs, grid-stride over (node, group)
                 long long want = (total + 255) / 256;
-                long long cap = (long long)resident_ctas(kern, 256, sm4) * 152;
+                long long cap = (long long)resident_ctas(kern, 256, sm4) * sm_count();
                 const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
                 kern<<<g4, 256, sm4, L.st>>>(static_cast<char*>(out), beta, sign, static_cast<const char*>(X),
                                              nb, xsb, csplit, N, s);

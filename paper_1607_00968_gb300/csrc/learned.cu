@@ -400,7 +400,8 @@ template <int CIN, int COUT>
 void wgrad_launch(const Launch& L, const __nv_bfloat16* x, const __nv_bfloat16* gy, int B, int H, int W,
                   float* dw, float* db) {
     long long ntiles = (long long)B * ((W + CTW - 1) / CTW) * ((H + CTH - 1) / CTH);
-    int grid = (int)(ntiles < 2 * 152 ? ntiles : 2 * 152);
+    const long long gcap = 2LL * sm_count();
+    int grid = (int)(ntiles < gcap ? ntiles : gcap);
     double px = (double)B * H * W;
     L.pre(KID_CONV_WGRAD, px * 2.0 * (CIN + COUT), 2.0 * px * 9 * CIN * COUT);
     k_conv_wgrad<CIN, COUT><<<grid, 256, 0, L.st>>>(x, gy, B, H, W, dw, db);
@@ -483,7 +484,7 @@ void launch_learned_residual(const Launch& L, const FineOp<float>& op, const c12
     k_learned_residual<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(op, f, z, r, s);
     L.post();
     L.pre(KID_LAYOUT, n * 8.0, n * 4.0);
-    k_colsumsq_c64<<<2 * 152, 256, 0, L.st>>>(r, op.g.N, s, rho2);
+    k_colsumsq_c64<<<2 * sm_count(), 256, 0, L.st>>>(r, op.g.N, s, rho2);
     L.post();
     L.pre(KID_LAYOUT, 8.0 * s, 0);
     k_rms<<<(s + 255) / 256, 256, 0, L.st>>>(rho2, s, (int)op.g.N, rho);

@@ -780,7 +780,9 @@ void launch_coldot(const Launch& L, const cplx<T>* a, const cplx<T>* b, long lon
                    double2* out, double2* part, unsigned int* count) {
     L.pre(KID_LAYOUT, 2.0 * N * s * cb<T>(), 8.0 * N * s);
     long long want = (N + 255) / 256;
-    k_coldot<T><<<(unsigned)(want < kColdotBlocks ? (want < 1 ? 1 : want) : kColdotBlocks), 256, 0, L.st>>>(
+    long long cap = 2LL * sm_count();
+    if (cap > kColdotBlocks) cap = kColdotBlocks;
+    k_coldot<T><<<(unsigned)(want < cap ? (want < 1 ? 1 : want) : cap), 256, 0, L.st>>>(
         a, b, N, s, out, part, count);
     L.post();
 }

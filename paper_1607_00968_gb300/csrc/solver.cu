@@ -42,6 +42,16 @@ thread_local std::string g_thread_error;
 constexpr double kDepAngle = 1e-7;
 constexpr double kDepRoundoff = 1e-12;
 
+// Orthogonalisation with orth = 0: one Gram-Schmidt pass and one Cholesky QR
+// pass, each repeated only when its rounding could leave the new basis block
+// less orthogonal than kOrthTarget.  One classical Gram-Schmidt pass leaves
+// components along the old basis of about u / sin(theta) of the column
+// (theta: its angle to the old basis), which the Cholesky QR multiplies by
+// at most kappa(W'); one Cholesky QR pass leaves an orthogonality error of
+// about u kappa(W')^2.  u is the unit roundoff of the Gram and update
+// arithmetic: 2^-53 in FP64, 2^-46 for the float-pair (double-float) kernels.
+constexpr double kOrthTarget = 1e-11;
+
 struct Level {
     Grid g;
     c128* coef = nullptr;    // K-point stencil of M_l (FP64)
@@ -190,6 +200,9 @@ struct helm_ctx {
     // K-cycle: per-CTA partial column products and the completion counter
     double2* kpart = nullptr;
     unsigned int* kcount = nullptr;
+    // orthogonalisation counters (helm_orth_stats): block QRs factored, and
+    // how many of them needed a second Gram-Schmidt / Cholesky QR pass
+    long long orth_qr = 0, orth_reorth = 0, orth_qr2 = 0;
 
     Launch L() { return Launch{st, &launches, prof}; }
     long long N() const { return lv[0].g.N; }
@@ -687,6 +700,67 @@ void cgs2(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H1, c128* H2) {
     }
 }
 
+// One Gram-Schmidt pass of the block at W against V_0..V_{nb-1} (orth = 0):
+// H = V^H W in full FP64-class precision, W -= V H.  A repeated pass's
+// coefficients are the rounding error of the first (about u / sin(theta) of
+// the column), so on the float-pair basis its update forms the product in
+// FP32 from the hi planes and adds it to the pairs exactly.
+void gs_pass(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H, bool repeat) {
+    const long long N = c->N();
+    const long long vs = N * s;
+    helm::launch_gram_f(c->L(), c->V, c->kfmt, nb, vs, Wp, c->kfmt, N, s, sb, c->partial, H,
+                        emulated(c), false);
+    helm::launch_combine_f(c->L(), Wp, c->kfmt, 1.0, -1.0, c->V, c->kfmt, nb, vs, H, N, s, sb,
+                           emulated(c), c->csplit, repeat && c->kfmt == helm::FMT_DD);
+}
+
+// Unit roundoff of the Gram and update arithmetic (see kOrthTarget).
+double orth_unit(const helm_ctx* c) { return emulated(c) ? std::ldexp(1.0, -46) : std::ldexp(1.0, -53); }
+
+// kappa_F(R) = ||R||_F ||R^{-1}||_F over the independent columns: an upper
+// bound of the 2-norm condition number (at most n times it).
+double kappa_f(const std::vector<cd>& R, const std::vector<cd>& T, int n) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < n * n; ++k) { a += std::norm(R[k]); b += std::norm(T[k]); }
+    return std::sqrt(a * b);
+}
+
+// After one Gram-Schmidt pass (orth = 0): does any group need a second?
+// Per group, from the QR Gram G = W'^H W' (already on the host) and ref2
+// (the squared norm each column lost to V): sin^2(theta_k) = G_kk /
+// (G_kk + ref2_k), and the pass is repeated when u / sin(theta_min) times
+// kappa_F(W') exceeds kOrthTarget (a column with no remainder always asks).
+bool needs_second_gs(const helm_ctx* c, int s, int sb, const std::vector<double>& ref2) {
+    const int G = (s + sb - 1) / sb;
+    const SmallLayout SL = small_layout(c, s, sb);
+    const cd* hG = reinterpret_cast<const cd*>(c->hsmall + SL.oG);
+    const double u = orth_unit(c);
+    for (int g = 0; g < G; ++g) {
+        const int n = std::min(sb, s - g * sb);
+        std::vector<cd> Gg((size_t)n * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) Gg[a * n + b] = hG[(size_t)g * sb * sb + a * sb + b];
+        double smin2 = 1.0;
+        std::vector<double> r2(n, 0.0);
+        for (int k = 0; k < n; ++k) {
+            const double gkk = Gg[k * n + k].real();
+            const double tot = gkk + ref2[g * sb + k];
+            if (!(tot > 0.0)) continue;           // zero column: nothing to orthogonalise
+            if (!(gkk > 0.0)) return true;
+            smin2 = std::min(smin2, gkk / tot);
+            r2[k] = tot;
+        }
+        std::vector<cd> R, T;
+        std::vector<int> dep;
+        chol_dep(Gg.data(), r2.data(), n, R, T, dep, true);
+        for (int k = 0; k < n; ++k)
+            if (dep[k] && r2[k] > 0.0) return true;
+        const double kf = kappa_f(R, T, n);
+        if (!(u / std::sqrt(smin2) * kf <= kOrthTarget)) return true;
+    }
+    return false;
+}
+
 // Factor the block at Win (already orthogonal to V_0..V_{nb-1}) as Vout R.
 // extra2: per column, the squared norm removed by that orthogonalisation
 // (sum of |H_ik|^2), so that extra2 + ||W_k||^2 is the column's squared norm
@@ -718,6 +792,7 @@ helm_status block_qr(helm_ctx* c, c128* Win, int wfmt, c128* Vout, int nb, int s
     out.R.assign(G, {});
     std::vector<std::vector<cd>> R1(G), R2(G);
     std::vector<int> mask(s, 0);
+    bool second = false;   // a second Cholesky QR pass is needed
     // pass 1
     helm_status st = HELM_OK;
     if (!gram_enqueued) {
@@ -744,8 +819,25 @@ helm_status block_qr(helm_ctx* c, c128* Win, int wfmt, c128* Vout, int nb, int s
                 hT[(size_t)g * sb * sb + a * sb + b] = (a < n && b < n) ? T[a * n + b] : cd(0.0);
         for (int k = 0; k < n; ++k)
             if (dep[k]) { mask[g * sb + k] = 1; any_dep = true; }
+        const double kf = kappa_f(R1[g], T, n);
+        if (!(orth_unit(c) * kf * kf <= kOrthTarget)) second = true;
     }
     CUDA_TRY(c, cudaMemcpyAsync(dT, hT, sizeof(c128) * SL.blk, cudaMemcpyHostToDevice, c->st));
+    c->orth_qr++;
+    if (c->p.orth == 0 && !second && !any_dep) {
+        // one Cholesky QR pass is accurate enough: Vout = Win R1^{-1}
+        helm::launch_combine_f(c->L(), Vout, c->kfmt, 0.0, 1.0, Win, wfmt, 1, 0, dT, N, s, sb, emulated(c),
+                               c->csplit);
+        for (int g = 0; g < G; ++g) {
+            const int n = std::min(sb, s - g * sb);
+            std::vector<cd> Rg((size_t)sb * sb, 0.0);
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) Rg[a * sb + b] = R1[g][a * n + b];
+            out.R[g] = Rg;
+        }
+        return HELM_OK;
+    }
+    c->orth_qr2++;
     helm::launch_combine_f(c->L(), c->W2, c->kfmt, 0.0, 1.0, Win, wfmt, 1, 0, dT, N, s, sb, emulated(c),
                            c->csplit);
     if (any_dep) {
@@ -902,9 +994,15 @@ helm_status fgmres_step_launches(helm_ctx* c, int j, int s, int sb) {
         helm::launch_apply<double, ZT, double, helm::FineOp<double>>(c->L(), fine_op<double>(c, false), Zj,
                                                                      c->W, s);
     }
-    cgs2(c, c->W, j + 1, s, sb, c->small + SL.oH1, c->small + SL.oH2);
-    CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * 2 * SL.oH2, cudaMemcpyDeviceToHost,
-                                c->st));
+    if (c->p.orth == 1) {
+        cgs2(c, c->W, j + 1, s, sb, c->small + SL.oH1, c->small + SL.oH2);
+        CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * 2 * SL.oH2, cudaMemcpyDeviceToHost,
+                                    c->st));
+    } else {
+        gs_pass(c, c->W, j + 1, s, sb, c->small + SL.oH1, false);
+        CUDA_TRY(c, cudaMemcpyAsync(c->hsmall, c->small, sizeof(c128) * (j + 1) * SL.blk,
+                                    cudaMemcpyDeviceToHost, c->st));
+    }
     return qr_gram_launch(c, c->W, c->kfmt, s, sb);
 }
 
@@ -1032,23 +1130,43 @@ helm_status fgmres_run(helm_ctx* c, int s, double tol, helm_info* info) {
             if (st != HELM_OK) return st;
             st = sync(c);
             if (st != HELM_OK) return st;
-            // H_{i,j} = H1 + H2 per group, and the reference norms
+            // H_{i,j} = H1 (+ H2 of a second pass) per group, and the
+            // reference norms (the squared norm each column lost to V)
             std::vector<double> ref2(s, 0.0);
             std::vector<std::vector<cd>> hcol(G);
             const int ld = (m + 1) * sb;
-            for (int g = 0; g < G; ++g) hcol[g].assign((size_t)ld * sb, 0.0);
-            for (int i = 0; i <= j; ++i)
-                for (int g = 0; g < G; ++g) {
-                    const int ng = std::min(sb, s - g * sb);   // columns of a ragged last group
-                    for (int a = 0; a < ng; ++a)
-                        for (int b = 0; b < ng; ++b) {
-                            long long o = ((long long)i * G + g) * sb * sb + a * sb + b;
-                            cd h = cd(c->hsmall[SL.oH1 + o].re, c->hsmall[SL.oH1 + o].im) +
-                                   cd(c->hsmall[SL.oH2 + o].re, c->hsmall[SL.oH2 + o].im);
-                            hcol[g][(size_t)b * ld + i * sb + a] = h;
-                            ref2[g * sb + b] += std::norm(h);
-                        }
-                }
+            bool two = c->p.orth == 1;
+            auto gather_h = [&]() {
+                std::fill(ref2.begin(), ref2.end(), 0.0);
+                for (int g = 0; g < G; ++g) hcol[g].assign((size_t)ld * sb, 0.0);
+                for (int i = 0; i <= j; ++i)
+                    for (int g = 0; g < G; ++g) {
+                        const int ng = std::min(sb, s - g * sb);   // columns of a ragged last group
+                        for (int a = 0; a < ng; ++a)
+                            for (int b = 0; b < ng; ++b) {
+                                long long o = ((long long)i * G + g) * sb * sb + a * sb + b;
+                                cd h = cd(c->hsmall[SL.oH1 + o].re, c->hsmall[SL.oH1 + o].im);
+                                if (two) h += cd(c->hsmall[SL.oH2 + o].re, c->hsmall[SL.oH2 + o].im);
+                                hcol[g][(size_t)b * ld + i * sb + a] = h;
+                                ref2[g * sb + b] += std::norm(h);
+                            }
+                    }
+            };
+            gather_h();
+            if (c->p.orth == 0 && needs_second_gs(c, s, sb, ref2)) {
+                // the single pass may have left too much of W along V: a
+                // second pass on the updated block, then its QR Gram again
+                c->orth_reorth++;
+                gs_pass(c, c->W, j + 1, s, sb, c->small + SL.oH2, true);
+                CUDA_TRY(c, cudaMemcpyAsync(c->hsmall + SL.oH2, c->small + SL.oH2,
+                                            sizeof(c128) * (j + 1) * SL.blk, cudaMemcpyDeviceToHost, c->st));
+                st = qr_gram_launch(c, c->W, c->kfmt, s, sb);
+                if (st != HELM_OK) return st;
+                st = sync(c);
+                if (st != HELM_OK) return st;
+                two = true;
+                gather_h();
+            }
             // W = V_{j+1} H_{j+1,j}
             st = block_qr(c, c->W, c->kfmt, c->V + (long long)(j + 1) * vs, j + 1, s, sb, ref2, qr, dep,
                           true);
@@ -1355,6 +1473,7 @@ void helm_default_params(helm_params* p) {
     p->cycle_gamma = 1;
     p->krylov = 0;
     p->graphs = 2;
+    p->orth = 0;
 }
 
 helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_params* p,
@@ -1372,6 +1491,7 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         return fail(nullptr, HELM_ERR_ARG, "the learned stage needs a 2D grid and learned_weights");
     if (p->cycle_gamma < 1 || p->cycle_gamma > 3 || (p->krylov != 0 && p->krylov != 1))
         return fail(nullptr, HELM_ERR_ARG, "cycle_gamma must be 1, 2 or 3, krylov 0 or 1");
+    if (p->orth != 0 && p->orth != 1) return fail(nullptr, HELM_ERR_ARG, "orth must be 0 or 1");
     if (p->krylov == 1 && p->cycle_gamma == 3)
         return fail(nullptr, HELM_ERR_ARG, "the K-cycle is nonlinear: use it with FGMRES (krylov 0)");
     if (p->krylov == 1 && p->prec == HELM_MIXED_C64_LEARNED)
@@ -1790,6 +1910,14 @@ helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, i
 }
 
 long long helm_kernel_launches(const helm_ctx* c) { return c ? c->launches : 0; }
+
+helm_status helm_orth_stats(const helm_ctx* c, long long* qr, long long* reorth, long long* qr2) {
+    if (!c) return fail(nullptr, HELM_ERR_ARG, "ctx is null");
+    if (qr) *qr = c->orth_qr;
+    if (reorth) *reorth = c->orth_reorth;
+    if (qr2) *qr2 = c->orth_qr2;
+    return HELM_OK;
+}
 
 static const char* kKernelNames[helm::KID_COUNT] = {
     "apply_fine", "apply_coarse", "residual_fp64", "jacobi_fine", "jacobi_coarse",

@@ -26,6 +26,7 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_solve_batch", "helm_destroy", "helm_last_error", "helm_level_shape",
            "helm_apply", "helm_smooth", "helm_restrict_residual", "helm_prolong_add",
            "helm_coarse_solve", "helm_vcycle", "helm_get_operator", "helm_kernel_launches",
+           "helm_orth_stats",
            "helm_profile_enable", "helm_profile_select", "helm_profile_kernel_count",
            "helm_profile_kernel_name",
            "helm_profile_read", "helm_vcycle_noalloc", "helm_learned_layers",
@@ -44,7 +45,7 @@ class HelmParams(ctypes.Structure):
                 ("block", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("prec", ctypes.c_int), ("learned_weights", ctypes.c_void_p),
                 ("coarse_tf32x3", ctypes.c_int), ("cycle_gamma", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("graphs", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("graphs", ctypes.c_int), ("orth", ctypes.c_int)]
 
 
 class HelmInfo(ctypes.Structure):
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_vcycle_noalloc": (i, [vp, i, vp, vp, i]),
         "helm_get_operator": (i, [vp, i, vp]),
         "helm_kernel_launches": (ll, [vp]),
+        "helm_orth_stats": (i, [vp, P(ll), P(ll), P(ll)]),
         "helm_profile_enable": (i, [vp, i]),
         "helm_profile_select": (i, [vp, i]),
         "helm_profile_kernel_count": (i, []),
@@ -181,7 +183,7 @@ class Solver:
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
                  prec: str = "c128", stream=None, coarse_tf32x3: bool = False,
                  learned_weights=None, cycle: str = "V", krylov: str = "fgmres",
-                 graphs: str = "auto"):
+                 graphs: str = "auto", orth: str = "selective"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libhelm needs a CUDA device")
@@ -210,6 +212,7 @@ class Solver:
         p.cycle_gamma = {"V": 1, "W": 2, "K": 3}[cycle]
         p.krylov = {"fgmres": 0, "bicgstab": 1}[krylov]
         p.graphs = {"off": 0, "on": 1, "auto": 2}[graphs]
+        p.orth = {"selective": 0, "twice": 1}[orth]
         self.learned_weights = learned_weights        # keeps the blob alive
         p.learned_weights = _ptr(learned_weights) if learned_weights is not None else None
         self.params = p
@@ -244,6 +247,14 @@ class Solver:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.helm_kernel_launches(self.ctx))
+
+    def orth_stats(self) -> dict:
+        """Block QRs factored since set-up, and how many needed a second
+        Gram-Schmidt pass (reorth) or a second Cholesky QR pass (qr2)."""
+        qr, re, q2 = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(self.lib.helm_orth_stats(self.ctx, ctypes.byref(qr), ctypes.byref(re),
+                                             ctypes.byref(q2)))
+        return {"qr": qr.value, "reorth": re.value, "qr2": q2.value}
 
     # -- solves ----------------------------------------------------------
     def _block(self, Q):

@@ -1,9 +1,9 @@
 """helm_vcycle_noalloc against helm_vcycle, through the C-ABI.
 
 helm_vcycle_noalloc serves callers that cannot allocate device memory when
-they run the preconditioner (for instance while a stream is being captured
-into a CUDA graph, or under a framework allocator that owns the device): its
-level buffers live in a fixed device array inside libhelm.  Its result must
+they run the preconditioner (latency-bound loops that cannot afford the
+synchronisation an allocation may cause, or a framework allocator that owns
+the device): its level buffers live in a fixed device array inside libhelm.  Its result must
 equal helm_vcycle's on the same context and input, on consecutive calls (the
 array keeps the previous call's contents), and it must refuse a block that
 needs more than the array holds.  This file is named to run last.
