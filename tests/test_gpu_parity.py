@@ -489,12 +489,17 @@ def test_bench_configuration_8hz_matches_oracle(H):
     """The salt workload as the benchmark times it, at its hardest frequency
     (8 Hz): 513 x 257 nodes, 64 sources on the top row, complex64 cycle with
     the FP16 coarsest product on 8,385 nodes, 3 levels, V(2,2) Jacobi 0.8,
-    shift 0.2, block 4, restart 6, tol 1e-6.  Every column's true residual
-    by the oracle's FP64 operator is <= 1e-6, and four columns agree with
-    the oracle's own block FGMRES solved to 1e-10 within 1e-5."""
+    shift 0.2, block 4, restart 6.
+    - tol 1e-6 (the benchmark's): every column's true residual by the
+      oracle's FP64 operator is <= 1e-6, and the error per unit residual
+      of four columns is no worse than that of the oracle's own block FGMRES
+      stopped at the same tolerance (at 8 Hz the error is ~50x the residual
+      for both: a property of the operator, not of the arithmetic);
+    - tol 1e-10: the same four columns agree with the oracle's solution to
+      1e-10 within 1e-5 (solution parity)."""
     P = I.salt2d_problem(seed=0, freq_hz=8.0)
     S = H.Solver(P.m, P.gamma, P.h, P.omega, shift=0.2, levels=3, block=4, restart=6, prec="c64",
-                 max_restarts=100)
+                 max_restarts=200)
     Q = P.rhs()
     U, info, st = S.solve(dev(Q), tol=1e-6)
     U = U.cpu().numpy()
@@ -504,8 +509,22 @@ def test_bench_configuration_8hz_matches_oracle(H):
     np.testing.assert_allclose(info.relres, rr, rtol=1e-6, atol=1e-13)
     cols = [0, 21, 42, 63]
     So = O.Solver(P.m, P.gamma, P.omega, P.h, levels=3, shift=0.2)
-    Uo, _ = So.solve(Q[cols].T.copy(), tol=1e-10, restart=6, block=4)
-    err = [rel(U[k], Uo[:, i]) for i, k in enumerate(cols)]
-    print("bench configuration 8 Hz: max relres %.3e, cycles %s, error vs oracle %s"
-          % (rr.max(), sorted(set(info.iters.tolist())), ["%.2e" % e for e in err]))
-    assert max(err) <= 1e-5, err
+    Ut, _ = So.solve(Q[cols].T.copy(), tol=1e-10, restart=6, block=4)
+    Uo6, _ = So.solve(Q[cols].T.copy(), tol=1e-6, restart=6, block=4)
+    err6 = [rel(U[k], Ut[:, i]) for i, k in enumerate(cols)]
+    err6_oracle = [rel(Uo6[:, i], Ut[:, i]) for i in range(len(cols))]
+    rr6_oracle = O.relres(A, Uo6, Q[cols].T)
+    U10, info10, _ = S.solve(dev(Q[cols]), tol=1e-10)
+    U10 = U10.cpu().numpy()
+    assert np.all(O.relres(A, U10.T, Q[cols].T) <= 1e-10)
+    err10 = [rel(U10[i], Ut[:, i]) for i in range(len(cols))]
+    print("bench configuration 8 Hz: max relres %.3e, cycles %s; error at tol 1e-6 %s (oracle's "
+          "own at 1e-6: %s); error at tol 1e-10 %s"
+          % (rr.max(), sorted(set(info.iters.tolist())), ["%.2e" % e for e in err6],
+             ["%.2e" % e for e in err6_oracle], ["%.2e" % e for e in err10]))
+    assert max(err10) <= 1e-5, err10
+    # error per unit residual: the GPU's no larger than the oracle's own
+    # (within a factor 3 for the different stopping points)
+    amp = max(e / rr[k] for e, k in zip(err6, cols))
+    amp_oracle = max(e / r for e, r in zip(err6_oracle, rr6_oracle))
+    assert amp <= 3.0 * amp_oracle, (err6, err6_oracle, amp, amp_oracle)
