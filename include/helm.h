@@ -97,9 +97,14 @@ typedef struct {
     int coarse_tf32x3;       /* complex64 coarsest solve on the tensor cores:
                                 0 = one FP16 product (11 significant bits,
                                 power-of-two scales of the inverse and of
-                                each right-hand side; ~1e-3 relative),
+                                each right-hand side; ~1e-3 relative) on the
+                                5th-generation tensor cores (tcgen05.mma,
+                                TMA-fed shared memory, accumulator in tensor
+                                memory);
                                 1 = three tf32 products on hi/lo splits
-                                (FP32-class)                                    */
+                                (FP32-class, mma.sync);
+                                2 = the FP16 product of 0 on mma.sync tiles
+                                (the earlier kernel, kept for comparison)    */
     int cycle_gamma;         /* 1 = V-cycle, 2 = W-cycle (two coarse visits per
                                 level, Sec. 4), 3 = K-cycle (Sec. 5.3: each
                                 coarse system solved by two flexible Krylov

@@ -17,7 +17,10 @@
 // range is split over CTAs so that the ~nc/128 row tiles fill the SMs.
 #include <cuda_fp16.h>
 
+#include <mutex>
+
 #include "kernels.h"
+#include "tc05.cuh"
 
 namespace helm {
 
@@ -409,6 +412,157 @@ __global__ void __launch_bounds__(256) k_dense_f16(const __half* __restrict__ A,
         }
 }
 
+// ---------------------------------------------------------------------------
+// FP16 product on the 5th-generation tensor cores (tcgen05)
+// ---------------------------------------------------------------------------
+// One CTA computes a 128 x 128 tile of C' (rows m0.., columns n0..) over its
+// K slice: a producer thread streams 64-wide K tiles of A'_h and of Bt into
+// shared memory with TMA (128-byte swizzle, UST stages, mbarrier
+// transaction counts), one thread issues tcgen05.mma M=128 N=128 K=16 with
+// the FP32 accumulator in 128 columns of tensor memory and frees each stage
+// with tcgen05.commit, and the four warps read the accumulator back with
+// tcgen05.ld (warp w owns rows 32w .. 32w+31) and write the K slice's
+// partial.  Rows beyond M and K beyond Kp are zero-filled by TMA.
+constexpr int UM = 128, UN = 128, UK = 64, UST = 6;
+constexpr uint32_t kUStageA = UM * UK * 2, kUStageB = UN * UK * 2, kUStage = kUStageA + kUStageB;
+constexpr size_t kUSmem = (size_t)UST * kUStage + 1024;   // + slack for 1024-byte alignment
+
+__device__ int g_dense_tc_error = 0;   // set when a pipeline wait gave up
+
+__global__ void __launch_bounds__(128, 1) k_dense_f16_tc05(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, int M,
+                                                           int kchunk, int Kp, float* __restrict__ P,
+                                                           int ldp) {
+    using namespace tc05;
+    extern __shared__ unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[UST], empty[UST], done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const uint32_t sraw = smem_u32(dsm);
+    const uint32_t sbase = (sraw + 1023u) & ~1023u;
+    unsigned char* tiles = dsm + (sbase - sraw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * UM, ks = blockIdx.y, n0 = blockIdx.z * UN;
+    const int k0 = ks * kchunk;
+    const int k1 = min(Kp, k0 + kchunk);
+    const int nk = k1 > k0 ? (k1 - k0 + UK - 1) / UK : 0;
+    volatile int* ab = &abort_flag;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < UST; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&done, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+        prefetch_tensormap(&tmA);
+        prefetch_tensormap(&tmB);
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, UN);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer: stage st of K tile kt is refilled once the MMAs that read
+        // it in the previous round have completed
+        int issued = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % UST;
+            if (kt >= UST && !mbar_wait(&empty[st], ((kt / UST) & 1) ^ 1, ab)) {
+                *ab = 1;
+                break;
+            }
+            unsigned char* a = tiles + (size_t)st * kUStage;
+            mbar_arrive_expect_tx(&full[st], kUStage);
+            tma_load_2d(a, &tmA, k0 + kt * UK, m0, &full[st]);
+            tma_load_2d(a + kUStageA, &tmB, k0 + kt * UK, n0, &full[st]);
+            issued = kt + 1;
+        }
+        if (*ab)   // let the copies this thread started land before the CTA exits
+            for (int kt = issued > UST ? issued - UST : 0; kt < issued; ++kt)
+                mbar_wait(&full[kt % UST], (kt / UST) & 1, nullptr);
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = idesc_f16_f32(UM, UN);
+        for (int kt = 0; kt < nk; ++kt) {
+            const int st = kt % UST;
+            if (!mbar_wait(&full[st], (kt / UST) & 1, ab)) {
+                *ab = 1;
+                break;
+            }
+            fence_after_sync();
+            const uint32_t a = sbase + (uint32_t)st * kUStage;
+            const uint32_t b = a + kUStageA;
+#pragma unroll
+            for (int k = 0; k < UK / 16; ++k)
+                umma_f16(tmem, sdesc_k128(a + k * 32), sdesc_k128(b + k * 32), idesc, (kt | k) != 0 ? 1u : 0u);
+            mma_commit(&empty[st]);
+        }
+        mma_commit(&done);   // arrives when every MMA issued above has completed
+    }
+    __syncwarp();
+    const bool ok = mbar_wait(&done, 0, nullptr) && !*ab;
+    __syncwarp();
+    fence_after_sync();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < UN / 32; ++c) {
+            float v[32];
+            if (nk > 0) {
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+            } else {   // an empty K slice contributes zero
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = 0.f;
+            }
+            if (row < M) {
+                float4* dst = reinterpret_cast<float4*>(P + ((size_t)ks * M + row) * ldp + n0 + c * 32);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(&g_dense_tc_error, 1);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, UN);
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2D FP16 tensor map of a row-major `rows` x `cols` matrix (row pitch
+// `pitch` elements), 64 x 128 boxes, 128-byte swizzle, zero fill outside
+bool map_f16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch) {
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+    cuuint32_t box[2] = {(cuuint32_t)UK, 128};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // u[row][j] = (sum over K slices of C') / (scale_A scale_j)
 __global__ void k_reduce_cprime_h(const float* __restrict__ P, int KS, int M, int ldp, int s,
                                   const float* __restrict__ ascale, const unsigned int* __restrict__ colmax,
@@ -451,6 +605,36 @@ int dense_tc_ksplit(int nc, int s) {
     }
     return best;
 }
+// K split of the tcgen05 product: one 193 KB CTA per SM, 64-wide K tiles;
+// the same cost model (waves x K tiles per CTA + reduction passes)
+int dense_tc05_ksplit(int nc, int s) {
+    const int mt = (nc + UM - 1) / UM, nt = dense_tc_ldb(s) / UN;
+    const int kt = (dense_tc_kpad(nc) + UK - 1) / UK;
+    const long long slots = sm_count();
+    int best = 1;
+    double best_cost = 1e300;
+    for (int ks = 1; ks <= kMaxKSplit; ++ks) {
+        long long ctas = (long long)mt * nt * ks;
+        long long waves = (ctas + slots - 1) / slots;
+        double cost = (double)waves * ((kt + ks - 1) / ks) + 0.45 * ks * nt;
+        if (cost < best_cost) { best_cost = cost; best = ks; }
+    }
+    return best;
+}
+
+int dense_tc_take_error(cudaStream_t st) {
+    static int zero = 0;
+    int e = 0;
+    if (cudaMemcpyFromSymbolAsync(&e, g_dense_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return 0;
+    if (e) {
+        cudaMemcpyToSymbolAsync(g_dense_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+    }
+    return e;
+}
+
 size_t dense_tc_scratch_floats(int nc, int s) {
     // B' (FP32, or FP16 B'^T in the first half), the K-slice partials, the
     // column scales of the FP16 path
@@ -478,8 +662,11 @@ void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, b
 }
 
 void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
-                     float* scratch, bool split3) {
-    const int Kp = dense_tc_kpad(nc), ldb = dense_tc_ldb(s), KS = dense_tc_ksplit(nc, s);
+                     float* scratch, int mode) {
+    const bool split3 = mode == 1;
+    const bool tc05 = mode == 0;
+    const int Kp = dense_tc_kpad(nc), ldb = dense_tc_ldb(s);
+    const int KS = tc05 ? dense_tc05_ksplit(nc, s) : dense_tc_ksplit(nc, s);
     float* Bp = scratch;
     float* P = scratch + (size_t)Kp * ldb;
     long long nb = (long long)Kp * ldb;
@@ -500,6 +687,30 @@ void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64
         }
         k_build_bt_h<<<(unsigned)((nb + 255) / 256), 256, 0, L.st>>>(f, nc, s, colmax, Bt, Kp, ldb);
         L.post();
+        if (tc05) {
+            CUtensorMap ta, tb;
+            const bool mapped = map_f16(&ta, Ah, Kp, nc, Kp) && map_f16(&tb, Bt, Kp, ldb, Kp);
+            const int kt = (Kp + UK - 1) / UK;
+            const int kchunk = ((kt + KS - 1) / KS) * UK;
+            dim3 grid((nc + UM - 1) / UM, KS, ldb / UN);
+            cudaFuncSetAttribute(k_dense_f16_tc05, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUSmem);
+            L.pre(KID_DENSE, 2.0 * nc * (double)Kp + 2.0 * nb + 4.0 * KS * nc * (double)ldb,
+                  8.0 * nc * (double)nc * s);
+            if (mapped) {
+                k_dense_f16_tc05<<<grid, 128, kUSmem, L.st>>>(ta, tb, nc, kchunk, Kp, P, ldb);
+            } else {
+                // no driver entry point for tensor maps: report it through the
+                // kernel's error flag (the solve then returns HELM_ERR_CUDA)
+                int one = 1;
+                cudaMemcpyToSymbolAsync(g_dense_tc_error, &one, sizeof(int), 0, cudaMemcpyHostToDevice, L.st);
+            }
+            L.post();
+            L.pre(KID_LAYOUT, 4.0 * KS * nc * 2.0 * s + 8.0 * nc * s, 0);
+            k_reduce_cprime_h<<<(unsigned)(((long long)nc * s + 255) / 256), 256, 0, L.st>>>(P, KS, nc, ldb, s,
+                                                                                              ascale, colmax, u);
+            L.post();
+            return;
+        }
         int kchunk = ((Kp / HBK + KS - 1) / KS) * HBK;
         dim3 grid((nc + HBM_ - 1) / HBM_, KS, ldb / HBN);
         size_t smem = sizeof(__half) * (size_t)HST * (HBM_ + HBN) * HLD;

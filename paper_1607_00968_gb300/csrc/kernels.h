@@ -77,7 +77,14 @@ void launch_build_aprime(const Launch& L, const c128* Minv, int nc, float* Ap, b
 // tf32 products on hi/lo splits (FP32-class accuracy); otherwise one FP16
 // product (11 significant bits, scaled per right-hand side)
 void launch_dense_tc(const Launch& L, const float* Ap, int nc, const c64* f, c64* u, int s,
-                     float* scratch, bool split3);
+                     float* scratch, int mode);
+// mode of launch_dense_tc: 0 = FP16 product on tcgen05 (TMA-fed, TMEM
+// accumulator), 1 = three tf32 products (mma.sync), 2 = FP16 product on
+// mma.sync (the earlier kernel, kept for comparison)
+int dense_tc05_ksplit(int nc, int s);
+// 1 if a tcgen05 coarsest product gave up waiting on its pipeline (or could
+// not build its tensor maps) since the last call; clears the flag
+int dense_tc_take_error(cudaStream_t st);
 
 // ---------------- learned stage (learned.cu) ----------------
 

@@ -293,8 +293,7 @@ void restrict_level(helm_ctx* c, int l, const cplx<T>* u, const cplx<FT>* f, cpl
 template <typename T>
 void coarsest(helm_ctx* c, const cplx<T>* f, cplx<T>* u, int s) {
     if constexpr (std::is_same<T, float>::value)
-        helm::launch_dense_tc(c->L(), c->Ap, c->nc, f, u, s, c->dense_scratch,
-                              c->p.coarse_tf32x3 != 0);
+        helm::launch_dense_tc(c->L(), c->Ap, c->nc, f, u, s, c->dense_scratch, c->p.coarse_tf32x3);
     else
         helm::launch_dense_apply<T>(c->L(), c->Minv, c->nc, f, u, s);
 }
@@ -654,6 +653,17 @@ struct QRResult {
 helm_status sync(helm_ctx* c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->st));
     CUDA_TRY(c, cudaGetLastError());
+    return HELM_OK;
+}
+
+// sync(), then report a tcgen05 coarsest product (complex64 cycle, default
+// product) that gave up waiting on its pipeline during the call
+helm_status sync_checked(helm_ctx* c) {
+    helm_status st = sync(c);
+    if (st != HELM_OK) return st;
+    if (c->p.coarse_tf32x3 == 0 && helm::dense_tc_take_error(c->st))
+        return fail(c, HELM_ERR_CUDA, "coarsest tensor-core product: a pipeline wait gave up after 1 s, "
+                                      "or its tensor maps could not be built");
     return HELM_OK;
 }
 
@@ -1422,7 +1432,7 @@ helm_status solve_internal(helm_ctx* c, const c128* Qd, int s, double tol, c128*
     if (st == HELM_ERR_ARG || st == HELM_ERR_CUDA || st == HELM_ERR_NOMEM || st == HELM_ERR_BREAKDOWN)
         return st;
     helm::launch_from_internal(c->L(), c->X, Ud, N, s, conjugate);
-    helm_status st2 = sync(c);
+    helm_status st2 = sync_checked(c);
     if (st2 != HELM_OK) return st2;
     return st;
 }
@@ -1492,6 +1502,8 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
     if (p->cycle_gamma < 1 || p->cycle_gamma > 3 || (p->krylov != 0 && p->krylov != 1))
         return fail(nullptr, HELM_ERR_ARG, "cycle_gamma must be 1, 2 or 3, krylov 0 or 1");
     if (p->orth != 0 && p->orth != 1) return fail(nullptr, HELM_ERR_ARG, "orth must be 0 or 1");
+    if (p->coarse_tf32x3 < 0 || p->coarse_tf32x3 > 2)
+        return fail(nullptr, HELM_ERR_ARG, "coarse_tf32x3 must be 0, 1 or 2");
     if (p->krylov == 1 && p->cycle_gamma == 3)
         return fail(nullptr, HELM_ERR_ARG, "the K-cycle is nonlinear: use it with FGMRES (krylov 0)");
     if (p->krylov == 1 && p->prec == HELM_MIXED_C64_LEARNED)
@@ -1599,7 +1611,7 @@ helm_status helm_setup(const double* m, const double* gamma_tilde, const helm_pa
         helm::launch_gauss_jordan<double>(L, dense, aug, n, factor, piv, pivval, dstatus, c->Minv);
     else
         helm::launch_gauss_jordan<float>(L, dense, aug, n, factor, piv, pivval, dstatus, c->Minv);
-    helm::launch_build_aprime(L, c->Minv, n, c->Ap, p->coarse_tf32x3 != 0);
+    helm::launch_build_aprime(L, c->Minv, n, c->Ap, p->coarse_tf32x3 == 1);
     int hstatus = 0;
     SETUP_TRY(cudaMemcpyAsync(&hstatus, dstatus, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     SETUP_TRY(cudaStreamSynchronize(c->st));
@@ -1783,7 +1795,7 @@ helm_status helm_coarse_solve(helm_ctx* c, int prec, const void* f, void* u, int
     if (st != HELM_OK) return st;
     if (prec == 0) coarsest<double>(c, static_cast<const c128*>(f), static_cast<c128*>(u), s);
     else coarsest<float>(c, static_cast<const c64*>(f), static_cast<c64*>(u), s);
-    return sync(c);
+    return sync_checked(c);
 }
 
 helm_status helm_vcycle(helm_ctx* c, int prec, const void* f, void* z, int s) {
@@ -1793,7 +1805,7 @@ helm_status helm_vcycle(helm_ctx* c, int prec, const void* f, void* z, int s) {
     if (st != HELM_OK) return st;
     if (prec == 0) cycle<double, double>(c, 0, static_cast<const c128*>(f), static_cast<c128*>(z), s);
     else cycle<float, double>(c, 0, static_cast<const c128*>(f), static_cast<c64*>(z), s);
-    return sync(c);
+    return sync_checked(c);
 }
 
 helm_status helm_get_operator(const helm_ctx* c, int level, void* coef_host) {
@@ -1900,7 +1912,7 @@ helm_status helm_vcycle_noalloc(helm_ctx* c, int prec, const void* f, void* z, i
     }
     if (prec == 0) cycle<double, double>(c, 0, static_cast<const c128*>(f), static_cast<c128*>(z), s);
     else cycle<float, double>(c, 0, static_cast<const c128*>(f), static_cast<c64*>(z), s);
-    st = sync(c);
+    st = sync_checked(c);
     for (size_t l = 0; l < c->lv.size(); ++l) {
         c->lv[l].u0 = saved[l][0]; c->lv[l].u1 = saved[l][1];
         c->lv[l].e = saved[l][2];  c->lv[l].f = saved[l][3];

@@ -182,6 +182,7 @@ class Solver:
                  levels: int = 3, pre: int = 2, post: int = 2, jacobi_w: float = 0.8,
                  restart: int = 10, block: int = 8, max_restarts: int = 50,
                  prec: str = "c128", stream=None, coarse_tf32x3: bool = False,
+                 coarse: str = "fp16",
                  learned_weights=None, cycle: str = "V", krylov: str = "fgmres",
                  graphs: str = "auto", orth: str = "selective"):
         import torch
@@ -208,7 +209,8 @@ class Solver:
         p.levels, p.pre, p.post, p.jacobi_w = int(levels), int(pre), int(post), float(jacobi_w)
         p.restart, p.block, p.max_restarts = int(restart), int(block), int(max_restarts)
         p.prec = PREC[prec]
-        p.coarse_tf32x3 = 1 if coarse_tf32x3 else 0
+        # complex64 coarsest product: "fp16" (tcgen05), "tf32x3", "fp16_mma_sync"
+        p.coarse_tf32x3 = 1 if coarse_tf32x3 else {"fp16": 0, "tf32x3": 1, "fp16_mma_sync": 2}[coarse]
         p.cycle_gamma = {"V": 1, "W": 2, "K": 3}[cycle]
         p.krylov = {"fgmres": 0, "bicgstab": 1}[krylov]
         p.graphs = {"off": 0, "on": 1, "auto": 2}[graphs]
