@@ -46,8 +46,8 @@ def dd_peak_tflops(sms: int, sm_mhz: float) -> float:
 # over the profiler's algorithmic bytes, per kernel class (the Grams read
 # exactly their operands; part of an update's written lines are still in L2
 # when it ends).  Valid while these kernels are unchanged.
-TRAFFIC_RATIO = {"gram_dd": (1.001, "profiles/traffic_salt2d_512x256_5hz.md"),
-                 "combine_dd": (0.923, "profiles/traffic_salt2d_512x256_5hz.md")}
+TRAFFIC_RATIO = {"gram_dd": (1.002, "profiles/dd_traffic_salt2d_512x256_16src_5hz.md"),
+                 "combine_dd": (0.740, "profiles/dd_traffic_salt2d_512x256_16src_5hz.md")}
 
 # solver parameters of the workload (Sec. 5.3: V(2,2) weighted Jacobi 0.8)
 SOLVER = dict(pre=2, post=2, jacobi_w=0.8)

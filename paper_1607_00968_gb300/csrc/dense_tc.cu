@@ -605,8 +605,10 @@ int dense_tc_ksplit(int nc, int s) {
     }
     return best;
 }
-// K split of the tcgen05 product: one 193 KB CTA per SM, 64-wide K tiles;
-// the same cost model (waves x K tiles per CTA + reduction passes)
+// K split of the tcgen05 product: one 193 KB CTA per SM, 64-wide K tiles.
+// Cost in K-tile times: waves x (K tiles per CTA + a CTA's fixed cost:
+// barrier and tensor-memory set-up, pipeline fill, epilogue, about nine
+// K tiles as measured at 30 tiles per CTA) + the reduction passes.
 int dense_tc05_ksplit(int nc, int s) {
     const int mt = (nc + UM - 1) / UM, nt = dense_tc_ldb(s) / UN;
     const int kt = (dense_tc_kpad(nc) + UK - 1) / UK;
@@ -616,7 +618,7 @@ int dense_tc05_ksplit(int nc, int s) {
     for (int ks = 1; ks <= kMaxKSplit; ++ks) {
         long long ctas = (long long)mt * nt * ks;
         long long waves = (ctas + slots - 1) / slots;
-        double cost = (double)waves * ((kt + ks - 1) / ks) + 0.45 * ks * nt;
+        double cost = (double)waves * ((kt + ks - 1) / ks + 9.0) + 0.45 * ks * nt;
         if (cost < best_cost) { best_cost = cost; best = ks; }
     }
     return best;

@@ -187,6 +187,8 @@ bool dd_formats_ok(int s, int sb);
 // Block Gram per group:  out[i][g][a][b] = sum_node conj(X_i[node][g*sb+a]) Y[node][g*sb+b]
 // for i < nb (X_i = X + i*xstride).  partial: scratch of gram_partial_elems().
 long long gram_partial_elems(long long N, int nb, int s, int sb);
+// bytes at the start of that scratch that must be zero before its first use
+long long gram_scratch_zero_bytes();
 // emulate: double-float arithmetic on the FP32 pipes instead of FP64.
 void launch_gram(const Launch& L, const c128* X, int nb, long long xstride, const c128* Y,
                  long long N, int s, int sb, c128* partial, c128* out, bool emulate);

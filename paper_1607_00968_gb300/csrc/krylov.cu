@@ -125,6 +125,62 @@ __global__ void __launch_bounds__(32 * kReduceWarps) k_gram_reduce(const c128* _
     }
 }
 
+// Two-stage form of the same sum in one launch.  CTA (g, p) of a grid of
+// ceil(E/32) x P covers entries 32g .. 32g+31: warp w adds the chunks
+// p + P w, p + P (w + 8), ... in increasing order, the eight warps are added
+// in warp order and the CTA writes red2[p][e]; the last of the P CTAs of
+// entry group g to finish (counter count[g], reset by it) adds red2[0..P-1]
+// in order.  The order of every sum is fixed, so the result does not depend
+// on scheduling.
+constexpr int kReduceSplit = 16;        // most CTAs along the chunks of one entry group
+constexpr int kReduceCounters = 16384;  // entry groups of 32 covered by the counters
+constexpr long long kReduceReserve = kReduceCounters * sizeof(unsigned int) / sizeof(c128);
+__global__ void __launch_bounds__(256) k_gram_reduce2(const c128* __restrict__ partial, int chunks, long long E,
+                                                      c128* __restrict__ red2, unsigned int* __restrict__ count,
+                                                      c128* __restrict__ out) {
+    __shared__ double2 red[8][32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x, part = blockIdx.y, P = gridDim.y;
+    const long long e = (long long)g * 32 + lane;
+    double re = 0.0, im = 0.0;
+    if (e < E) {
+#pragma unroll 4
+        for (int c = part + P * w; c < chunks; c += 8 * P) {
+            const c128 v = partial[(long long)c * E + e];
+            re += v.re;
+            im += v.im;
+        }
+    }
+    red[w][lane] = make_double2(re, im);
+    __syncthreads();
+    if (w == 0) {
+        for (int k = 1; k < 8; ++k) { re += red[k][lane].x; im += red[k][lane].y; }
+        if (P == 1) {
+            if (e < E) out[e] = mk(re, im);
+        } else if (e < E) {
+            red2[(long long)part * E + e] = mk(re, im);
+        }
+    }
+    if (P == 1) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count + g, 1u) == (unsigned int)(P - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (w == 0 && e < E) {
+        double sr = 0.0, si = 0.0;
+        for (int q = 0; q < P; ++q) {
+            const double2 v = __ldcg(reinterpret_cast<const double2*>(red2 + (long long)q * E + e));
+            sr += v.x;
+            si += v.y;
+        }
+        out[e] = mk(sr, si);
+    }
+    if (threadIdx.x == 0) count[g] = 0u;
+}
+
 template <typename TX>
 __global__ void __launch_bounds__(kThreads) k_combine(c128* __restrict__ out, double beta, double sign,
                                                        const cplx<TX>* __restrict__ X, int nb,
@@ -635,16 +691,16 @@ template <int XF, int OF>
 __global__ void __launch_bounds__(256) k_combine_sb4(char* __restrict__ out, double beta, double sign,
                                                       const char* __restrict__ X, int nb,
                                                       long long xstride,
-                                                      const float4* __restrict__ Cs, long long N,
+                                                      const c128* __restrict__ C, long long N,
                                                       int s) {
     extern __shared__ float4 cs4[];                // nb x 4 x 4 x G
     const int G = s / 4;
     const int nc = nb * G * 16;
     for (int idx = threadIdx.x; idx < nc; idx += blockDim.x) {
-        // source [i][g][a][b] -> [i][a][b][g]
+        // source [i][g][a][b] -> [i][a][b][g], split into float pairs
         int i = idx / (G * 16), rem = idx - i * G * 16;
         int g = rem / 16, ab = rem - g * 16;
-        cs4[(i * 16 + ab) * G + g] = Cs[idx];
+        cs4[(i * 16 + ab) * G + g] = split_c(C[idx]);
     }
     __syncthreads();
     const long long plane = N * s;
@@ -731,7 +787,7 @@ __global__ void __launch_bounds__(256) k_combine_sb4(char* __restrict__ out, dou
 __global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, const char* __restrict__ base,
                                                          double sign, const char* __restrict__ X, int nb,
                                                          long long xstride,
-                                                         const float4* __restrict__ Cs, long long N,
+                                                         const c128* __restrict__ C, long long N,
                                                          int s) {
     extern __shared__ float2 cs2[];                // nb x 4 x 4 x G, (re hi, im hi)
     const int G = s / 4;
@@ -739,7 +795,7 @@ __global__ void __launch_bounds__(256) k_combine_sb4_hi(char* __restrict__ out, 
     for (int idx = threadIdx.x; idx < nc; idx += blockDim.x) {
         int i = idx / (G * 16), rem = idx - i * G * 16;
         int g = rem / 16, ab = rem - g * 16;
-        const float4 c = Cs[idx];
+        const float4 c = split_c(C[idx]);
         cs2[(i * 16 + ab) * G + g] = make_float2(c.x, c.z);
     }
     __syncthreads();
@@ -999,11 +1055,16 @@ __global__ void k_fill_random(char* Xb, long long N, int s, const int* __restric
 
 }  // namespace
 
+// Layout of the Gram scratch: the reduction's counters (kReduceReserve
+// elements, zero at allocation and left zero by every launch), the chunk
+// partials, the reduction's per-part sums.
 long long gram_partial_elems(long long N, int nb, int s, int sb) {
     int G = (s + sb - 1) / sb;
     long long E1 = (long long)G * sb * sb;
-    return (long long)gram_chunks(N, nb, s) * nb * E1;
+    return kReduceReserve + (long long)gram_chunks(N, nb, s) * nb * E1 + (long long)kReduceSplit * nb * E1;
 }
+
+long long gram_scratch_zero_bytes() { return kReduceReserve * (long long)sizeof(c128); }
 
 // CTAs of `kern` resident per SM at this launch shape (at least 1)
 template <typename K>
@@ -1043,8 +1104,10 @@ void gram_dd_dispatch(int xf, int yf, dim3 grid, size_t sm, cudaStream_t st, con
 }  // namespace
 
 void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xstride, const void* Y,
-                   int yf, long long N, int s, int sb, c128* partial, c128* out, bool emulate,
+                   int yf, long long N, int s, int sb, c128* scratch, c128* out, bool emulate,
                    bool hi_only) {
+    unsigned int* counters = reinterpret_cast<unsigned int*>(scratch);
+    c128* partial = scratch + kReduceReserve;
     int G = (s + sb - 1) / sb;
     long long E1 = (long long)G * sb * sb;
     int chunks = gram_chunks(N, nb, s);
@@ -1125,7 +1188,16 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
     L.post();
     long long E = E1 * nb;
     L.pre(KID_GRAM_REDUCE, (chunks + 1.0) * E * 16.0, 2.0 * chunks * E);
-    k_gram_reduce<<<(unsigned)((E + 31) / 32), 32 * kReduceWarps, 0, L.st>>>(partial, chunks, E, out);
+    const long long groups = (E + 31) / 32;
+    if (groups <= kReduceCounters) {
+        int P = chunks / 16;
+        P = P < 1 ? 1 : (P > kReduceSplit ? kReduceSplit : P);
+        c128* red2 = partial + (long long)chunks * E;
+        k_gram_reduce2<<<dim3((unsigned)groups, (unsigned)P), 256, 0, L.st>>>(partial, chunks, E, red2, counters,
+                                                                             out);
+    } else {
+        k_gram_reduce<<<(unsigned)groups, 32 * kReduceWarps, 0, L.st>>>(partial, chunks, E, out);
+    }
     L.post();
 }
 
@@ -1159,9 +1231,6 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
         const long long gcap = 16LL * sm_count();
         int grid = (int)(ntiles < gcap ? ntiles : gcap);
         long long nc = (long long)nb * G * sb * sb;
-        L.pre(KID_LAYOUT, 32.0 * nc, 0);
-        k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
-        L.post();
         if (hi_only && sb == 4 && s % 4 == 0 && xf == FMT_DD && of == FMT_DD && beta == 1.0 &&
             (size_t)nb * G * 16 * sizeof(float2) <= 160 * 1024) {
             L.pre(KID_COMBINE_HI, (double)N * s * (nb * 8.0 + 32.0), 8.0 * nb * (double)N * s * sb);
@@ -1175,7 +1244,7 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
             k_combine_sb4_hi<<<g4, 256, sm2, L.st>>>(static_cast<char*>(out),
                                                      static_cast<const char*>(base ? base : out), sign,
                                                      static_cast<const char*>(X), nb,
-                                                     xstride * fmt_bytes(xf), csplit, N, s);
+                                                     xstride * fmt_bytes(xf), C, N, s);
             L.post();
             return;
         }
@@ -1192,7 +1261,7 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
                 long long cap = (long long)resident_ctas(kern, 256, sm4) * sm_count();
                 const int g4 = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
                 kern<<<g4, 256, sm4, L.st>>>(static_cast<char*>(out), beta, sign, static_cast<const char*>(X),
-                                             nb, xsb, csplit, N, s);
+                                             nb, xsb, C, N, s);
             };
             if (of == FMT_DD) {
                 if (xf == FMT_DD) go(k_combine_sb4<FMT_DD, FMT_DD>);
@@ -1206,6 +1275,10 @@ void launch_combine_f(const Launch& L, void* out, int of, double beta, double si
             L.post();
             return;
         }
+        // general group sizes: the coefficients are split once beforehand
+        L.pre(KID_LAYOUT, 32.0 * nc, 0);
+        k_split<<<blocks_for(nc), kThreads, 0, L.st>>>(C, csplit, nc);
+        L.post();
         if (of == FMT_DD) {
             if (xf == FMT_DD) combine_dd_go<FMT_DD, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);
             else if (xf == FMT_C64) combine_dd_go<FMT_C64, FMT_DD>(L, grid, smem, out, beta, sign, X, nb, xsb, csplit, N, s, sb);

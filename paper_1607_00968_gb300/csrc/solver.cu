@@ -481,6 +481,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     pe = std::max(pe, helm::gram_partial_elems(N, 1, s, sb));
     c->partial_elems = pe;
     CUDA_TRY(c, dalloc(&c->partial, sizeof(c128) * pe));
+    CUDA_TRY(c, cudaMemsetAsync(c->partial, 0, (size_t)helm::gram_scratch_zero_bytes(), c->st));
     // small: 2 H passes + G + T + Y + norms
     long long blk = (long long)G * sb * sb;
     c->small_elems = std::max(2 * (m + 1) * blk + 2 * blk + (long long)m * blk, 10 * blk) + 4LL * s + 64;
