@@ -293,8 +293,8 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------
 
-def make_solvers(helm, probs, prec, args):
-    kw = dict(SOLVER, levels=args.levels)
+def make_solvers(helm, probs, prec, args, **extra):
+    kw = dict(SOLVER, levels=args.levels, **extra)
     return [helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, restart=args.restart,
                         block=args.block, prec=prec, max_restarts=100, **kw) for P in probs]
 
@@ -314,6 +314,30 @@ def timed_steps(torch, solvers, Qd, steps, stream):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b), infos
+
+
+def learned_arm(helm, torch, probs, Qd, stream, args):
+    """One step of the workload with the learned stage after every V-cycle
+    (weights trained on seeded models disjoint from this one)."""
+    from paper_1607_00968_gb300 import learned
+    path = os.path.join(ROOT, "paper_1607_00968_gb300", "weights", "learned_salt2d.bin")
+    try:
+        net = learned.Network.load(path)
+    except (OSError, ValueError) as e:
+        return {"value": None, "unit": UNIT, "what": "weights not loadable: %s" % e}
+    ls = make_solvers(helm, probs, "learned", args, learned_weights=net.blob)
+    for S in ls:
+        S.solve(Qd, TOL)
+    lms, linfos = timed_steps(torch, ls, Qd, 1, stream)
+    for S in ls:
+        S.close()
+    conv = all(bool(np.all(i.relres <= TOL)) for i in linfos)
+    return {"value": NSRC * len(FREQS_HZ) / (lms / 1e3) if conv else None, "unit": UNIT, "ms_per_step": lms,
+            "cycles": [int(np.max(i.iters)) for i in linfos],
+            "max_relres": float(max(np.max(i.relres) for i in linfos)), "converged": conv,
+            "training": net.record.get("loss", "error of the cycle"),
+            "what": "complex64 cycle + learned BF16 stage (6 conv 3x3, 32 channels) after every cycle, "
+                    "kept per column only where it lowers the residual"}
 
 
 # --------------------------------------------------------------------------
@@ -599,6 +623,11 @@ def main():
         for S in ps:
             S.close()
 
+    # ---------------- the learned stage beside it (same workload) ----------------
+    lrn = None
+    if not args.no_plain:
+        lrn = learned_arm(helm, torch, probs, Qd, stream, args)
+
     # ---------------- the paper's fastest variant beside it: W-BiCG ----------------
     wbicg = None
     if not args.no_plain:
@@ -652,7 +681,8 @@ def main():
             "status": "ok" if converged else "not converged: a column ended above tol (value withheld)",
             "cycles_per_frequency": iters, "max_relres": relres, "orth": orth,
             "oracle_check": oracle_check,
-            "roofline": roof, "kernels": kernels, "plain": plain, "w_bicg": wbicg, "eikonal": eik,
+            "roofline": roof, "kernels": kernels, "plain": plain, "learned": lrn, "w_bicg": wbicg,
+            "eikonal": eik,
             "speedup_vs_plain": round(value / plain["value"], 3) if (plain and converged) else None,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks,

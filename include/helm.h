@@ -337,6 +337,28 @@ helm_status helm_adam(float* p, const float* g, float* m, float* v, void* p_bf16
    [s][N2][N1][16].  Allocates its own temporaries. */
 helm_status helm_learned_input(helm_ctx* ctx, const void* f, const void* z, int s, void* x_out,
                                float* rho_out);
+/* Residual-loss training inputs for a block (not in the paper; the loss of
+   helm_learned_residual_loss): as helm_learned_input, plus, per sample j in
+   NHWC image order [s][N2][N1], r_out = r / rho_j and coef_out = h^2 c_A =
+   kappa (1 - i gamma), both as float pairs (re, im).  Allocates its own
+   temporaries. */
+helm_status helm_learned_residual_input(helm_ctx* ctx, const void* f, const void* z, int s, void* x_out,
+                                        float* rho_out, float* r_out, float* coef_out);
+/* Residual of the corrected iterate as the training loss (not in the paper):
+   with e_b = pred_b channels (0, 1) as a complex image and K = h^2 A on the
+   image grid (K e = 4 e - the four neighbours (zero outside) - coef e),
+       q_b = r_b - K e_b,   loss = mean_b ||q_b||^2 / ||r_b||^2,
+   grad (bf16 [B][H][W][16], channels 0, 1) = -(2 / (B ||r_b||^2)) K^H q_b
+   (K^H uses conj(coef)).  pred: float [B][H][W][16]; r, coef: float pairs
+   [B][H][W]; q: float-pair scratch [B][H][W]; sums: 2B floats of scratch;
+   loss_out: device float.  All device pointers; enqueued on stream and
+   synchronised. */
+helm_status helm_learned_residual_loss(const float* pred, const float* r, const float* coef, int batch, int H,
+                                       int W, float* q, float* sums, void* grad, float* loss_out,
+                                       void* stream);
+/* v[node][j] = r[j][node] as complex128: an image-order block of float pairs
+   [s][N] to the internal layout (the next vector of a training chain). */
+helm_status helm_learned_image_to_block(const float* r, long long N, int s, void* v, void* stream);
 /* Training target t[j][node][0..1] = scale * e[node][j] / rho[j] (e complex64,
    internal layout); scale = 1/h^2 makes it the network's output units. */
 helm_status helm_learned_target(const void* e, long long N, int s, const float* rho, float scale,

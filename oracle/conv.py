@@ -93,3 +93,49 @@ def loss_grad(pred: np.ndarray, target: np.ndarray) -> np.ndarray:
     B = pred.shape[0]
     t2 = np.sum(target.reshape(B, -1) ** 2, axis=1).reshape(B, 1, 1, 1)
     return 2.0 * (pred - target) / t2 / B
+
+
+# --------------------------------------------------------------------------
+# residual loss of the corrected iterate
+# --------------------------------------------------------------------------
+
+def h2A_image(e: np.ndarray, coef: np.ndarray, adjoint: bool = False) -> np.ndarray:
+    """K e on each image of a batch (B, H, W) complex, K = h^2 A of the
+    Helmholtz operator (Sec. 2.1 Eq. helm in the library's sign) on the node
+    grid in image order (pixel (i, j) = node i W + j): the 5-point stencil
+    4 e - (the four neighbours, zero outside the grid) minus the mass term
+    coef e, coef = h^2 omega^2 m (1 - i gamma).  adjoint: K^H, the same
+    stencil with conj(coef)."""
+    ep = np.pad(e, ((0, 0), (1, 1), (1, 1)))
+    nb = ep[:, :-2, 1:-1] + ep[:, 2:, 1:-1] + ep[:, 1:-1, :-2] + ep[:, 1:-1, 2:]
+    c = np.conj(coef) if adjoint else coef
+    return 4.0 * e - nb - c * e
+
+
+def residual_loss(pred: np.ndarray, r: np.ndarray, coef: np.ndarray) -> float:
+    """mean_b ||r_b - K e_b||^2 / ||r_b||^2 with e_b = pred_b[..., 0] + i
+    pred_b[..., 1] (pred: (B, H, W, C), C >= 2), r and coef complex (B, H, W):
+    the residual left after adding the network's correction, relative to the
+    residual before it (the learned stage's output is in units of h^2 rho,
+    its input residual in units of rho)."""
+    e = pred[..., 0] + 1j * pred[..., 1]
+    q = r - h2A_image(e, coef)
+    B = pred.shape[0]
+    num = np.sum(np.abs(q.reshape(B, -1)) ** 2, axis=1)
+    den = np.sum(np.abs(r.reshape(B, -1)) ** 2, axis=1)
+    return float(np.mean(num / den))
+
+
+def residual_loss_grad(pred: np.ndarray, r: np.ndarray, coef: np.ndarray) -> np.ndarray:
+    """d residual_loss / d pred, channel by channel: for L_b = ||r - K e||^2
+    and e = a + i b, dL/da = -2 Re(K^H q) and dL/db = -2 Im(K^H q), scaled
+    by 1 / (B ||r_b||^2); zero in channels >= 2."""
+    e = pred[..., 0] + 1j * pred[..., 1]
+    q = r - h2A_image(e, coef)
+    B = pred.shape[0]
+    den = np.sum(np.abs(r.reshape(B, -1)) ** 2, axis=1).reshape(B, 1, 1)
+    g = -2.0 * h2A_image(q, coef, adjoint=True) / (B * den)
+    out = np.zeros_like(pred)
+    out[..., 0] = g.real
+    out[..., 1] = g.imag
+    return out

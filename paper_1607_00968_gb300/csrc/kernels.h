@@ -106,6 +106,13 @@ void launch_unpack_add(const Launch& L, const float* out, int N, int s, const fl
                        c64* z);
 // kappa[i] = Re(cA[i]) h^2 = omega^2 m_i h^2 (the network's third input channel)
 void launch_kappa(const Launch& L, const c128* cA, long long N, double h2, float* kappa);
+// residual-loss training inputs (image order, float pairs): r / rho and h^2 c_A
+void launch_pack_resid(const Launch& L, const c64* r, int N, int s, const float* rho, const c128* cA,
+                       double h2, float* rimg, float* cimg);
+// loss = mean_b ||rt_b - h^2 A pred_b||^2 / ||rt_b||^2 and its gradient (bf16, 16 channels)
+void launch_residual_loss(const Launch& L, const float* pred, const float* rt, const float* coef, int B, int H,
+                          int W, float* q, float* sums, void* grad, float* loss_out);
+void launch_image_to_block(const Launch& L, const float* rimg, long long N, int s, c128* v);
 void launch_pack_target(const Launch& L, const c64* e, int N, int s, const float* rho, float scale,
                         float* t);
 // loss = mean_b ||pred_b - t_b||^2 / ||t_b||^2 over channels 0, 1 (pred: 16-channel

@@ -491,6 +491,104 @@ void launch_learned_residual(const Launch& L, const FineOp<float>& op, const c12
     L.post();
 }
 
+// Residual-loss inputs, sample j in image order: rimg[j][node] = r[node][j] /
+// rho_j and cimg[j][node] = h^2 c_A[node] (= kappa (1 - i gamma)), float pairs
+__global__ void k_pack_resid(const c64* __restrict__ r, int N, int s, const float* __restrict__ rho,
+                             const c128* __restrict__ cA, double h2, float2* __restrict__ rimg,
+                             float2* __restrict__ cimg) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= (long long)N * s) return;
+    int node = (int)(k / s), j = (int)(k - (long long)node * s);
+    const float inv = rho[j] > 0.f ? 1.f / rho[j] : 0.f;
+    const c64 v = r[k];
+    const c128 c = cA[node];
+    rimg[(size_t)j * N + node] = make_float2(v.re * inv, v.im * inv);
+    cimg[(size_t)j * N + node] = make_float2((float)(c.re * h2), (float)(c.im * h2));
+}
+
+// K e at pixel (i, x) of sample b for K = h^2 A (or its adjoint, conj_c):
+// 4 e - (the four neighbours, zero outside) - c e; e given as float pairs
+// with a stride of `es` floats per pixel
+__device__ __forceinline__ float2 h2A_pixel(const float* __restrict__ e, int es, const float2* __restrict__ coef,
+                                            size_t base, int H, int W, int i, int x, bool conj_c) {
+    const size_t p = base + (size_t)i * W + x;
+    float re = 4.f * e[p * es], im = 4.f * e[p * es + 1];
+    if (i > 0) { re -= e[(p - W) * es]; im -= e[(p - W) * es + 1]; }
+    if (i + 1 < H) { re -= e[(p + W) * es]; im -= e[(p + W) * es + 1]; }
+    if (x > 0) { re -= e[(p - 1) * es]; im -= e[(p - 1) * es + 1]; }
+    if (x + 1 < W) { re -= e[(p + 1) * es]; im -= e[(p + 1) * es + 1]; }
+    const float2 c = coef[p];
+    const float ci = conj_c ? -c.y : c.y;
+    const float er = e[p * es], ei = e[p * es + 1];
+    re -= c.x * er - ci * ei;
+    im -= c.x * ei + ci * er;
+    return make_float2(re, im);
+}
+
+// q = rt - K pred (pred channels 0, 1 of 16), per sample num[b] += |q|^2,
+// den[b] += |rt|^2
+__global__ void k_rloss_q(const float* __restrict__ pred, const float2* __restrict__ rt,
+                          const float2* __restrict__ coef, int H, int W, float2* __restrict__ q,
+                          float* __restrict__ num, float* __restrict__ den) {
+    __shared__ float sn[256], sd[256];
+    const int b = blockIdx.y;
+    const long long P = (long long)H * W;
+    const size_t base = (size_t)b * P;
+    float an = 0.f, ad = 0.f;
+    for (long long p = blockIdx.x * 256LL + threadIdx.x; p < P; p += (long long)gridDim.x * 256) {
+        const int i = (int)(p / W), x = (int)(p - (long long)i * W);
+        const float2 ke = h2A_pixel(pred, 16, coef, base, H, W, i, x, false);
+        const float2 r = rt[base + p];
+        const float2 v = make_float2(r.x - ke.x, r.y - ke.y);
+        q[base + p] = v;
+        an += v.x * v.x + v.y * v.y;
+        ad += r.x * r.x + r.y * r.y;
+    }
+    sn[threadIdx.x] = an;
+    sd[threadIdx.x] = ad;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) { sn[threadIdx.x] += sn[threadIdx.x + w]; sd[threadIdx.x] += sd[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { atomicAdd(num + b, sn[0]); atomicAdd(den + b, sd[0]); }
+}
+
+// g = d loss / d pred = -(2 / (B den_b)) K^H q (channels 0, 1; zero beyond),
+// bf16 [B][H][W][16]; loss_out = mean_b num_b / den_b
+__global__ void k_rloss_grad(const float2* __restrict__ q, const float2* __restrict__ coef, int B, int H, int W,
+                             const float* __restrict__ num, const float* __restrict__ den,
+                             __nv_bfloat16* __restrict__ g, float* __restrict__ loss_out) {
+    const long long P = (long long)H * W;
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k == 0 && loss_out) {
+        float l = 0.f;
+        for (int b = 0; b < B; ++b) l += den[b] > 0.f ? num[b] / den[b] : 0.f;
+        *loss_out = l / B;
+    }
+    if (k >= (long long)B * P) return;
+    const int b = (int)(k / P);
+    const long long p = k - (long long)b * P;
+    const int i = (int)(p / W), x = (int)(p - (long long)i * W);
+    const float2 kh = h2A_pixel(reinterpret_cast<const float*>(q), 2, coef, (size_t)b * P, H, W, i, x, true);
+    const float c = den[b] > 0.f ? -2.f / (den[b] * B) : 0.f;
+    __nv_bfloat16* o = g + k * 16;
+    reinterpret_cast<__nv_bfloat162*>(o)[0] = __floats2bfloat162_rn(c * kh.x, c * kh.y);
+    __nv_bfloat162 z2 = __floats2bfloat162_rn(0.f, 0.f);
+#pragma unroll
+    for (int t = 1; t < 8; ++t) reinterpret_cast<__nv_bfloat162*>(o)[t] = z2;
+}
+
+// v[node][j] = rimg[j][node] as complex128 (image order -> internal block)
+__global__ void k_image_to_block(const float2* __restrict__ rimg, long long N, int s, c128* __restrict__ v) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= N * s) return;
+    long long node = k / s;
+    int j = (int)(k - node * s);
+    const float2 r = rimg[(size_t)j * N + node];
+    v[k] = mk((double)r.x, (double)r.y);
+}
+
 __global__ void k_kappa(const c128* __restrict__ cA, long long N, double h2, float* __restrict__ kappa) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i < N) kappa[i] = (float)(cA[i].re * h2);
@@ -499,6 +597,42 @@ __global__ void k_kappa(const c128* __restrict__ cA, long long N, double h2, flo
 void launch_kappa(const Launch& L, const c128* cA, long long N, double h2, float* kappa) {
     L.pre(KID_SETUP, 0, 0);
     k_kappa<<<(unsigned)((N + 255) / 256), 256, 0, L.st>>>(cA, N, h2, kappa);
+    L.post();
+}
+
+void launch_pack_resid(const Launch& L, const c64* r, int N, int s, const float* rho, const c128* cA,
+                       double h2, float* rimg, float* cimg) {
+    long long n = (long long)N * s;
+    L.pre(KID_LAYOUT, n * (8.0 + 16.0 + 16.0), 0);
+    k_pack_resid<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(r, N, s, rho, cA, h2,
+                                                                 reinterpret_cast<float2*>(rimg),
+                                                                 reinterpret_cast<float2*>(cimg));
+    L.post();
+}
+
+void launch_residual_loss(const Launch& L, const float* pred, const float* rt, const float* coef, int B, int H,
+                          int W, float* q, float* sums, void* grad, float* loss_out) {
+    const long long P = (long long)H * W;
+    cudaMemsetAsync(sums, 0, sizeof(float) * 2 * B, L.st);
+    dim3 grid((unsigned)((P + 255) / 256 < 64 ? (P + 255) / 256 : 64), B);
+    L.pre(KID_LAYOUT, (double)B * P * (64.0 + 8.0 + 8.0 + 8.0), (double)B * P * 20.0);
+    k_rloss_q<<<grid, 256, 0, L.st>>>(pred, reinterpret_cast<const float2*>(rt),
+                                      reinterpret_cast<const float2*>(coef), H, W, reinterpret_cast<float2*>(q),
+                                      sums, sums + B);
+    L.post();
+    const long long n = (long long)B * P;
+    L.pre(KID_LAYOUT, n * (8.0 + 8.0 + 32.0), n * 20.0);
+    k_rloss_grad<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(
+        reinterpret_cast<const float2*>(q), reinterpret_cast<const float2*>(coef), B, H, W, sums, sums + B,
+        static_cast<__nv_bfloat16*>(grad), loss_out);
+    L.post();
+}
+
+void launch_image_to_block(const Launch& L, const float* rimg, long long N, int s, c128* v) {
+    long long n = N * s;
+    L.pre(KID_LAYOUT, n * 24.0, 0);
+    k_image_to_block<<<(unsigned)((n + 255) / 256), 256, 0, L.st>>>(reinterpret_cast<const float2*>(rimg), N, s,
+                                                                     v);
     L.post();
 }
 

@@ -2037,6 +2037,39 @@ helm_status helm_learned_input(helm_ctx* c, const void* f, const void* z, int s,
     return st;
 }
 
+helm_status helm_learned_residual_input(helm_ctx* c, const void* f, const void* z, int s, void* x_out,
+                                        float* rho_out, float* r_out, float* coef_out) {
+    if (!c || !f || !z || !x_out || !rho_out || !r_out || !coef_out || s < 1 || c->p.dim != 2)
+        return fail(c, HELM_ERR_ARG, "bad arguments to helm_learned_residual_input");
+    c64* r = nullptr;
+    float* rho2 = nullptr;
+    CUDA_TRY(c, dalloc(&r, sizeof(c64) * (size_t)c->N() * s));
+    CUDA_TRY(c, dalloc(&rho2, sizeof(float) * s));
+    helm::launch_learned_residual(c->L(), fine_op<float>(c, false), static_cast<const c128*>(f),
+                                  static_cast<const c64*>(z), r, s, rho2, rho_out);
+    helm::launch_pack_input(c->L(), r, (int)c->N(), s, rho_out, c->kappa, x_out);
+    helm::launch_pack_resid(c->L(), r, (int)c->N(), s, rho_out, c->cA, c->p.h * c->p.h, r_out, coef_out);
+    helm_status st = sync(c);
+    dfree(r);
+    dfree(rho2);
+    return st;
+}
+
+helm_status helm_learned_residual_loss(const float* pred, const float* r, const float* coef, int batch, int H,
+                                       int W, float* q, float* sums, void* grad, float* loss_out,
+                                       void* stream) {
+    if (!pred || !r || !coef || !q || !sums || !grad || batch < 1 || H < 1 || W < 1)
+        return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_learned_residual_loss");
+    helm::launch_residual_loss(bare_launch(stream), pred, r, coef, batch, H, W, q, sums, grad, loss_out);
+    return check_launch(stream);
+}
+
+helm_status helm_learned_image_to_block(const float* r, long long N, int s, void* v, void* stream) {
+    if (!r || !v || N < 1 || s < 1) return fail(nullptr, HELM_ERR_ARG, "bad arguments to helm_learned_image_to_block");
+    helm::launch_image_to_block(bare_launch(stream), r, N, s, static_cast<c128*>(v));
+    return check_launch(stream);
+}
+
 helm_status helm_learned_target(const void* e, long long N, int s, const float* rho, float scale,
                                 float* t_out, void* stream) {
     if (!e || !rho || !t_out || N < 1 || s < 1)

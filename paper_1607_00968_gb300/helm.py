@@ -32,7 +32,8 @@ EXPORTS = ["helm_default_params", "helm_setup", "helm_solve", "helm_adjoint", "h
            "helm_profile_read", "helm_vcycle_noalloc", "helm_learned_layers",
            "helm_learned_blob_bytes", "helm_learned_layer", "helm_conv3x3", "helm_conv3x3_wgrad",
            "helm_conv3x3_flip", "helm_adam", "helm_learned_input", "helm_learned_target",
-           "helm_learned_loss", "helm_fields_to_half", "helm_fwi_jv", "helm_fwi_jtw",
+           "helm_learned_loss", "helm_learned_residual_input", "helm_learned_residual_loss",
+           "helm_learned_image_to_block", "helm_fields_to_half", "helm_fwi_jv", "helm_fwi_jtw",
            "helm_fwi_gradient", "helm_eik_create", "helm_eik_forward", "helm_eik_jv", "helm_eik_jtw",
            "helm_eik_last_error", "helm_eik_destroy"]
 
@@ -110,6 +111,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "helm_learned_input": (i, [vp, vp, vp, i, vp, vp]),
         "helm_learned_target": (i, [vp, ll, i, vp, ctypes.c_float, vp, vp]),
         "helm_learned_loss": (i, [vp, vp, i, ll, vp, vp, vp, vp]),
+        "helm_learned_residual_input": (i, [vp, vp, vp, i, vp, vp, vp, vp]),
+        "helm_learned_residual_loss": (i, [vp, vp, vp, i, i, i, vp, vp, vp, vp, vp]),
+        "helm_learned_image_to_block": (i, [vp, ll, i, vp, vp]),
         "helm_fields_to_half": (i, [vp, ll, i, vp, vp]),
         "helm_fwi_jv": (i, [vp, vp, i, i, vp, vp, i, d, vp]),
         "helm_fwi_jtw": (i, [vp, vp, i, i, vp, vp, i, d, vp]),

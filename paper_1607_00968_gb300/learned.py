@@ -9,11 +9,12 @@ loss and optimiser step runs in libhelm's kernels (helm_conv3x3,
 helm_conv3x3_wgrad, helm_conv3x3_flip, helm_learned_loss, helm_adam); this
 module holds the buffers and drives the loop.
 
-Training pairs come from the solver itself on seeded random faulted/salt
-models: for right-hand sides v taken along two chains started at the point
-sources (the residuals of the stationary iteration x <- x + V(b - A x), and a
-one-vector Arnoldi process on A V), the target is e = A^{-1} v - V(v), with
-A^{-1} v from a tight solve.
+Training data come from the solver itself on seeded random faulted/salt
+models.  Default loss: the residual left after the correction,
+||r - h^2 A (h^2 rho N)|| / ||r|| in the network's units (train_residual;
+the right-hand sides follow the stationary iteration's residual chain, and
+every pair costs one V-cycle, no solve).  Earlier loss: the error, target e
+= A^{-1} v - V(v) with A^{-1} v from a tight solve (make_pairs, train).
 
 Weights are saved as the flat blob of the ABI (bf16 weights + float biases)
 plus a JSON header (layer table, training record).
@@ -223,6 +224,133 @@ def make_pairs(seeds, freqs, cells=(512, 256), h=12.5, nsrc=32, steps=2, shift=0
     return torch.cat(xs), torch.cat(ts)
 
 
+# ----------------------------------------------------------------------
+# residual-loss training: the residual of the corrected iterate
+# ----------------------------------------------------------------------
+
+def residual_pairs(seed, freq, cells=(512, 256), h=12.5, nsrc=32, steps=16, shift=0.2, levels=3,
+                   width=20):
+    """(x bf16 [P, H, W, 16], r float [P, H, W, 2], coef float [P, H, W, 2]),
+    P = nsrc * steps, from one seeded random model at one frequency.
+
+    The right-hand sides follow the stationary iteration's residual chain,
+    v_{k+1} = (v_k - A V(v_k)) / rho_k, started at unit point sources: half
+    on the top node row (where the benchmark's sources sit), half at seeded
+    random interior nodes.  Every step runs in libhelm kernels (V-cycle,
+    residual, packing, the chain's next vector)."""
+    import torch
+    lib = helm.load()
+    P = inputs.random_problem_2d(seed, cells, h, freq, nsrc, width=width, levels=levels)
+    S = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=shift, levels=levels, block=8, restart=10,
+                    prec="c64", max_restarts=50)
+    H, W = P.shape
+    N = S.N
+    g = np.random.Generator(np.random.PCG64(7919 + seed))
+    top = inputs.line_positions(P.shape, nsrc - nsrc // 2, 0, width)
+    inner = [(int(g.integers(2, H - width)), int(g.integers(width, W - width)))
+             for _ in range(nsrc // 2)]
+    b = torch.as_tensor(inputs.point_sources(P.shape, top + inner, h)).cuda()   # (s, N)
+    v = b.T.contiguous()                                                         # (N, s) layout
+    xs, rs, cs = [], [], []
+    stream = _vp_stream(torch)
+    for _ in range(steps):
+        z1 = S.vcycle(v, "c64")
+        x = torch.empty((nsrc, H, W, 16), dtype=torch.bfloat16, device="cuda")
+        r = torch.empty((nsrc, H, W, 2), dtype=torch.float32, device="cuda")
+        c = torch.empty((nsrc, H, W, 2), dtype=torch.float32, device="cuda")
+        rho = torch.empty(nsrc, dtype=torch.float32, device="cuda")
+        st = lib.helm_learned_residual_input(S.ctx, _vp(v), _vp(z1), nsrc, _vp(x), _vp(rho), _vp(r), _vp(c))
+        if st != 0:
+            raise helm.HelmError(st, lib.helm_last_error(S.ctx).decode())
+        xs.append(x)
+        rs.append(r)
+        cs.append(c)
+        v = torch.empty((N, nsrc), dtype=torch.complex128, device="cuda")
+        st = lib.helm_learned_image_to_block(_vp(r), N, nsrc, _vp(v), stream)
+        if st != 0:
+            raise helm.HelmError(st, lib.helm_last_error(None).decode())
+    S.close()
+    return torch.cat(xs), torch.cat(rs), torch.cat(cs)
+
+
+class ResidualLoss:
+    """Scratch and the call of helm_learned_residual_loss for one batch shape."""
+
+    def __init__(self, batch, H, W, device="cuda"):
+        import torch
+        self.B, self.H, self.W = batch, H, W
+        self.q = torch.empty((batch, H, W, 2), dtype=torch.float32, device=device)
+        self.sums = torch.empty(2 * batch, dtype=torch.float32, device=device)
+        self.loss = torch.empty(1, dtype=torch.float32, device=device)
+        self.grad = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=device)
+        self.lib = helm.load()
+        self.torch = torch
+
+    def __call__(self, pred, r, c):
+        st = self.lib.helm_learned_residual_loss(_vp(pred), _vp(r), _vp(c), self.B, self.H, self.W, _vp(self.q),
+                                                 _vp(self.sums), _vp(self.grad), _vp(self.loss),
+                                                 _vp_stream(self.torch))
+        if st != 0:
+            raise helm.HelmError(st, self.lib.helm_last_error(None).decode())
+        return self.grad
+
+
+def evaluate_residual_loss(net: Network, x, r, c, batch=8):
+    """Mean residual loss over a pool (1 = the correction removes nothing)."""
+    P, H, W, _ = x.shape
+    rl = ResidualLoss(batch, H, W, device=x.device)
+    tot, n = 0.0, 0
+    for i0 in range(0, P - batch + 1, batch):
+        out = net.forward(x[i0:i0 + batch].contiguous(), batch, H, W)
+        rl(out, r[i0:i0 + batch].contiguous(), c[i0:i0 + batch].contiguous())
+        tot += float(rl.loss.item())
+        n += 1
+    return tot / max(n, 1)
+
+
+def train_residual(net: Network, configs, iters_per_config=64, batch=8, lr=1e-3, buffer_configs=4,
+                   seed=0, log_every=100, **pair_kw):
+    """Online training on the residual loss: the pairs of each (seed, freq)
+    configuration join a rolling buffer of the last `buffer_configs`
+    configurations, and `iters_per_config` Adam steps on batches drawn from
+    the buffer follow.  Returns the loss history."""
+    import torch
+    g = np.random.Generator(np.random.PCG64(seed))
+    buf = []
+    hist = []
+    it = 0
+    pairs = 0
+    t0 = time.perf_counter()
+    rl = None
+    for (sd, f) in configs:
+        buf.append(residual_pairs(sd, f, **pair_kw))
+        pairs += buf[-1][0].shape[0]
+        if len(buf) > buffer_configs:
+            buf.pop(0)
+        X = torch.cat([b[0] for b in buf])
+        R = torch.cat([b[1] for b in buf])
+        Cf = torch.cat([b[2] for b in buf])
+        P, H, W, _ = X.shape
+        if rl is None:
+            rl = ResidualLoss(batch, H, W, device=X.device)
+        for _ in range(iters_per_config):
+            idx = torch.as_tensor(g.choice(P, size=batch, replace=False), device=X.device)
+            xb, rb, cb = X[idx].contiguous(), R[idx].contiguous(), Cf[idx].contiguous()
+            out, acts = net.forward(xb, batch, H, W, keep=True)
+            grad = rl(out, rb, cb)
+            net.zero_grad()
+            net.backward(acts, grad, batch, H, W)
+            net.adam(lr=lr)
+            if it % log_every == 0:
+                hist.append((it, float(rl.loss.item())))
+            it += 1
+        del X, R, Cf
+    net.record.update(dict(loss="residual of the corrected iterate", iters=it, batch=batch, lr=lr,
+                           pairs=int(pairs), configs=[list(c) for c in configs],
+                           seconds=time.perf_counter() - t0, loss_history=hist))
+    return hist
+
+
 def train(net: Network, x, t, iters=400, batch=8, lr=1e-3, seed=0, log_every=50):
     """Adam on mini-batches of whole images; returns the loss history."""
     import torch
@@ -272,12 +400,28 @@ def evaluate_loss(net: Network, x, t, batch=8):
 
 def main():
     """Train the stage on seeded models and save the blob:
-    python -m paper_1607_00968_gb300.learned OUT_PATH [ITERS]"""
+    python -m paper_1607_00968_gb300.learned OUT_PATH [ITERS_PER_CONFIG] [error]
+    (default: the residual loss, online over 40 model/frequency
+    configurations, about 20k pairs; `error` selects the earlier error
+    loss with ITERS total steps)."""
     import sys
     import torch
     out = sys.argv[1] if len(sys.argv) > 1 else "learned_salt2d.bin"
-    iters = int(sys.argv[2]) if len(sys.argv) > 2 else 600
     torch.cuda.set_device(0)
+    if len(sys.argv) <= 3 or sys.argv[3] != "error":
+        ipc = int(sys.argv[2]) if len(sys.argv) > 2 else 64
+        configs = [(sd, f) for sd in range(101, 111) for f in (3.0, 4.5, 6.0, 7.5)]
+        net = Network(seed=0)
+        xv, rv, cv = residual_pairs(201, 5.0, nsrc=16, steps=8)
+        before = evaluate_residual_loss(net, xv, rv, cv)
+        train_residual(net, configs, iters_per_config=ipc)
+        after = evaluate_residual_loss(net, xv, rv, cv)
+        net.record.update(dict(val_loss_before=before, val_loss_after=after, val_seeds=[201],
+                               val_freq_hz=5.0, cells=[512, 256], h=12.5))
+        net.save(out)
+        print(json.dumps(net.record))
+        return
+    iters = int(sys.argv[2]) if len(sys.argv) > 2 else 600
     t0 = time.perf_counter()
     x, t = make_pairs(seeds=(101, 102, 103), freqs=(3.5, 5.0, 6.5), nsrc=32, steps=3)
     xv, tv = make_pairs(seeds=(201,), freqs=(5.0,), nsrc=16, steps=3)
