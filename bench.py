@@ -70,7 +70,7 @@ def parse():
                     choices=["salt2d", "layered2d", "layered3d", "batch"],
                     help="salt2d: the default line; the others are the small 2D, the 3D and the "
                          "uneven-batch configurations, measured with the same timing rules")
-    ap.add_argument("--problems", type=int, default=40, help="batch workload: number of problems")
+    ap.add_argument("--problems", type=int, default=200, help="batch workload: number of problems")
     return ap.parse_args()
 
 
@@ -423,38 +423,85 @@ def run_other(args):
     else:
         rng = np.random.Generator(np.random.PCG64(args.seed))
         grids = [(256, 128), (512, 256), (1024, 512)]
-        solvers, Qs, meta = [], [], []
+        specs = []
         for k in range(args.problems):
             cells = grids[rng.integers(0, 3)]
             f = float(rng.uniform(2.0, 10.0))
             s = int(rng.integers(1, 129))
             prec = "c64" if rng.uniform() < 0.5 else "c128"
             # fewest levels whose coarsest grid has <= 9000 nodes (dense
-            # inverse); the FP64 path keeps <= 2200 to bound its set-up
-            lv = inputs.default_levels(cells, 9000 if prec == "c64" else 2200)
-            P = inputs.random_problem_2d(1000 + k, cells, 12.5, f, s, width=20, levels=lv)
-            st = torch.cuda.Stream()
-            solvers.append(helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, levels=lv,
-                                       block=args.block, restart=args.restart, prec=prec,
-                                       max_restarts=300, stream=st))
-            Qs.append(torch.as_tensor(P.rhs()).cuda())
-            meta.append(dict(cells=cells, f=round(f, 2), s=s, prec=prec, levels=lv))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Us, infos, st = helm.solve_batch(solvers, Qs, TOL, check=False)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        tot = sum(q.shape[0] for q in Qs)
-        conv = sum(int(np.all(i.relres <= TOL)) for i in infos)
+            # inverse; five levels on the 1024 x 512 grid left the coarsest
+            # grid at ~8 radians per cell at 9 Hz, and those complex128
+            # problems stagnated even with K-cycles).  Hierarchies of four
+            # levels put the coarsest grid at more than ~2 radians per cell
+            # at the higher frequencies, where V-cycles stall: those
+            # problems use the K-cycle (Sec. 5.3).
+            lv = inputs.default_levels(cells, 9000)
+            specs.append(dict(k=k, cells=cells, f=round(f, 3), s=s, prec=prec, levels=lv,
+                              cycle="K" if lv >= 4 else "V"))
+        chunk = 40          # contexts alive at once (their Krylov workspaces share HBM)
+
+        def run_chunk(sp):
+            t0 = time.perf_counter()
+            solvers, Qs = [], []
+            for d in sp:
+                P = inputs.random_problem_2d(1000 + d["k"], d["cells"], 12.5, d["f"], d["s"], width=20,
+                                             levels=d["levels"])
+                st = torch.cuda.Stream()
+                solvers.append(helm.Solver(P.m, P.gamma, P.h, P.omega, shift=args.shift, levels=d["levels"],
+                                           block=args.block, restart=args.restart, prec=d["prec"],
+                                           cycle=d["cycle"], max_restarts=300, stream=st))
+                Qs.append(torch.as_tensor(P.rhs()).cuda())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            Us, infos, st = helm.solve_batch(solvers, Qs, TOL, check=False)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            for S in solvers:
+                S.close()
+            del solvers, Qs, Us
+            torch.cuda.empty_cache()    # give the cached blocks back: libhelm allocates with cudaMalloc
+            conv = [bool(np.all(i.relres <= TOL)) for i in infos]
+            cyc = [int(i.iters.max()) if i.iters.size else 0 for i in infos]
+            return t1 - t0, t2 - t1, conv, cyc, int(st)
+
+        setup_s = solve_s = 0.0
+        convs, cycles, status = [], [], 0
+        workers = os.environ.get("HELM_BATCH_WORKERS", "4")
+        first_s = None
+        for c0 in range(0, len(specs), chunk):
+            a, b, cv, cy, st = run_chunk(specs[c0:c0 + chunk])
+            if first_s is None:
+                first_s = b
+            setup_s += a
+            solve_s += b
+            convs += cv
+            cycles += cy
+            status = status or st
+        # the first chunk again with one host worker: what the streams buy
+        os.environ["HELM_BATCH_WORKERS"] = "1"
+        _, serial_s, _, _, _ = run_chunk(specs[:chunk])
+        os.environ["HELM_BATCH_WORKERS"] = workers
+        tot = sum(d["s"] for d in specs)
+        for d, c, cy in zip(specs, convs, cycles):
+            d["converged"] = c
+            d["cycles"] = cy
         line.update({"metric": "Helmholtz RHS-solves/s to rel-res 1e-6 (uneven batch of %d 2D problems)"
                                % args.problems,
-                     "value": round(tot / wall, 3), "ms_per_step": wall * 1e3, "steps": 1,
-                     "warmup": 0, "dtype": "mixed c64/c128",
+                     "value": round(tot / solve_s, 3) if all(convs) else None,
+                     "ms_per_step": solve_s * 1e3, "steps": 1, "warmup": 0, "dtype": "mixed c64/c128",
                      "config": dict(workload="batch%d_2d_uneven" % args.problems, rhs=tot,
                                     grids=grids, freq_hz=[2, 10], h=12.5, shift=args.shift,
-                                    block=args.block, restart=args.restart,
-                                    workers=int(os.environ.get("HELM_BATCH_WORKERS", "4"))),
-                     "converged_problems": conv, "status": int(st), "problems": meta})
+                                    block=args.block, restart=args.restart, workers=int(workers),
+                                    contexts_at_once=chunk,
+                                    cycle="V below four levels, K-cycle from four levels on"),
+                     "e2e": {"value": round(tot / (solve_s + setup_s), 3), "unit": UNIT,
+                             "what": "including each problem's set-up (hierarchy, coarsest inverse, "
+                                     "H2D of the model and of the right-hand sides)"},
+                     "streams_vs_one_worker": {"first_chunk_s_workers": round(first_s, 3),
+                                               "first_chunk_s_one_worker": round(serial_s, 3),
+                                               "speedup": round(serial_s / first_s, 3)},
+                     "converged_problems": int(sum(convs)), "status": status, "problems": specs})
     print(json.dumps(line))
 
 

@@ -277,12 +277,21 @@ __device__ __forceinline__ void dd_mac(float& S, float& L, float ah, float al, f
 }
 
 constexpr int kMaxQPT = 4;   // quads per thread; a quad is one row a and four columns b..b+3
+constexpr int kFlushNodes = 64;   // nodes a thread adds in float pairs before moving them to FP64
 
 // Same partition of the output as k_gram.  The quads (g, a, b0) are spread
 // over ceil(Q / qpt) threads; when that leaves threads over, R replicas of
 // that layout share the CTA and take every R-th node of a tile, and their
 // sums are added at the end.  The next node tile is loaded into registers
-// while the current one is being used.
+// while the current one is being used.  With more quads than one CTA holds
+// (Q > kThreads * QPT, e.g. blocks of 32 columns) the quads are cut into
+// gridDim.z consecutive parts of ceil(Q / gridDim.z), one CTA each; every
+// part then has more than kThreads * QPT / 2 quads, so R = 1, and each part
+// writes only its own quads' entries of the (chunk, block) slot.  Every
+// thread moves its float pairs into FP64 totals every kFlushNodes nodes: a
+// pair's correction term gathers one FP32 rounding per product, so long
+// runs (blocks of 32 columns leave one replica per quad, thousands of nodes
+// per thread) would lose the pair's precision.
 template <int QPT, int XF, int YF>
 __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X, long long xstride,
                                                        const char* __restrict__ Y, long long N,
@@ -298,9 +307,12 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X
     const int G = (s + sb - 1) / sb;
     const int nbq = (sb + 3) / 4;
     const long long E1 = (long long)G * sb * sb;
-    const int Q = G * sb * nbq;
-    const int nthr = (Q + qpt - 1) / qpt;         // threads per replica (<= kThreads)
-    const int R = kThreads / nthr;                // replicas
+    const int Qall = G * sb * nbq;
+    const int Qpart = (Qall + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int q0 = (int)blockIdx.z * Qpart;                      // this CTA's quads: [q0, q0 + Q)
+    const int Q = Qall - q0 < Qpart ? Qall - q0 : Qpart;
+    const int nthr = (Qpart + qpt - 1) / qpt;     // threads per replica (<= kThreads)
+    const int R = kThreads / nthr;                // replicas (1 whenever gridDim.z > 1)
     const int rep = threadIdx.x / nthr;
     const int qt = threadIdx.x - rep * nthr;
     const bool active = rep < R;
@@ -312,12 +324,16 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X
     c128* out = partial + ((long long)blockIdx.x * gridDim.y + i) * E1;
 
     float S[QPT][4][2], Lc[QPT][4][2];
+    double D[QPT][4][2];    // FP64 totals of the float pairs
+    int since = 0;
     int xa[QPT], yb[QPT], nv[QPT];
 #pragma unroll
     for (int q = 0; q < QPT; ++q) {
-        int id = qt + q * nthr;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) D[q][k][0] = D[q][k][1] = 0.0;
+        int id = q0 + qt + q * nthr;
         nv[q] = 0; xa[q] = 0; yb[q] = 0;
-        if (active && id < Q) {
+        if (active && id < q0 + Q) {
             int g = id / (sb * nbq);
             int rem = id - g * sb * nbq;
             int a = rem / nbq, b0 = (rem % nbq) * 4;
@@ -382,6 +398,19 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X
                 }
             }
         }
+        since += cur > rep ? (cur - rep + R - 1) / R : 0;
+        if (since >= kFlushNodes) {
+            since = 0;
+#pragma unroll
+            for (int q = 0; q < QPT; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        D[q][k][c] += f2d_bits(S[q][k][c]) + f2d_bits(Lc[q][k][c]);
+                        S[q][k][c] = Lc[q][k][c] = 0.f;
+                    }
+        }
     }
     // sum the replicas in FP64 through shared memory, then write every entry
     // of the output slot (zero outside a ragged last group)
@@ -394,15 +423,15 @@ __global__ void __launch_bounds__(kThreads) k_gram_dd(const char* __restrict__ X
     }
 #pragma unroll
     for (int q = 0; q < QPT; ++q) {
-        int id = qt + q * nthr;
-        if (!active || id >= Q) continue;
+        int id = q0 + qt + q * nthr;
+        if (!active || id >= q0 + Q) continue;
         int g = id / (sb * nbq);
         int rem = id - g * sb * nbq;
         int a = rem / nbq, b0 = (rem % nbq) * 4;
         for (int k = 0; k < 4 && b0 + k < sb; ++k) {
             long long e = ((long long)g * sb + a) * sb + b0 + k;
-            double re = k < nv[q] ? f2d_bits(S[q][k][0]) + f2d_bits(Lc[q][k][0]) : 0.0;
-            double im = k < nv[q] ? f2d_bits(S[q][k][1]) + f2d_bits(Lc[q][k][1]) : 0.0;
+            double re = k < nv[q] ? D[q][k][0] + (f2d_bits(S[q][k][0]) + f2d_bits(Lc[q][k][0])) : 0.0;
+            double im = k < nv[q] ? D[q][k][1] + (f2d_bits(S[q][k][1]) + f2d_bits(Lc[q][k][1])) : 0.0;
             if (use_red) red[(long long)rep * E1 + e] = make_double2(re, im);
             else out[e] = mk(re, im);
         }
@@ -1074,11 +1103,17 @@ int resident_ctas(K kern, int threads, size_t smem) {
     return n < 1 ? 1 : n;
 }
 
-bool gram_dd_ok(int s, int sb) {
+// quad parts of the double-float Gram (grid z): one CTA holds kThreads * kMaxQPT
+int gram_dd_parts(int s, int sb) {
     const int G = (s + sb - 1) / sb;
     const long long Q = (long long)G * sb * ((sb + 3) / 4);
-    return (Q + kThreads - 1) / kThreads <= kMaxQPT;
+    const long long per = (long long)kThreads * kMaxQPT;
+    return (int)((Q + per - 1) / per);
 }
+
+constexpr int kMaxGramParts = 8;
+
+bool gram_dd_ok(int s, int sb) { return gram_dd_parts(s, sb) <= kMaxGramParts; }
 
 bool combine_dd_ok(int s, int sb) {
     return s <= kThreads && (size_t)((kThreads / s) * kCombineRows * s + ((s + sb - 1) / sb) * sb * sb) *
@@ -1166,11 +1201,14 @@ void launch_gram_f(const Launch& L, const void* X, int xf, int nb, long long xst
         else go(k_gram_sb4<FMT_C128, FMT_C128>);
     } else if (dd) {
         const int nbq = (sb + 3) / 4;
-        const long long Q = (long long)G * sb * nbq;
+        const int parts = gram_dd_parts(s, sb);
+        const long long Qall = (long long)G * sb * nbq;
+        const long long Q = (Qall + parts - 1) / parts;      // quads per CTA
         int qpt = (int)((Q + kThreads - 1) / kThreads);
         if (qpt < 1) qpt = 1;
         int nthr = (int)((Q + qpt - 1) / qpt);
         int R = kThreads / nthr;
+        grid.z = parts;
         size_t red = R > 1 ? (size_t)R * E1 * sizeof(double2) : 0;
         size_t sm2 = smem > red ? smem : red;
         const char* Xb = static_cast<const char*>(X);

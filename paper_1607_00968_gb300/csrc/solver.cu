@@ -38,7 +38,14 @@ thread_local std::string g_thread_error;
 
 // A block column is dependent when its part orthogonal to the columns before
 // it has a sine below kDepAngle, or is below kDepRoundoff times the column's
-// norm before any orthogonalisation (same reading as the oracle).
+// norm before any orthogonalisation (same reading as the oracle).  The block
+// QR is a Cholesky QR, whose pivot for a column of sine t carries a relative
+// rounding error of about u / t^2: on the float-pair path (u = 2^-46) the
+// sine threshold is raised to 64 sqrt(u) = 7.6e-6, so that no column the
+// Cholesky factor cannot resolve is kept (measured: the restart blocks of 32
+// residuals on the 3D workload reach sines of 1e-5 .. 1e-7 as their columns
+// converge, and Cholesky factors of such blocks in float-pair arithmetic
+// broke the basis).
 constexpr double kDepAngle = 1e-7;
 constexpr double kDepRoundoff = 1e-12;
 
@@ -518,7 +525,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
 // dependence test; R upper triangular (row-major), T = R^{-1} on the
 // independent columns (zero rows/columns for dependent ones).
 bool chol_dep(const cd* G, const double* ref2, int n, std::vector<cd>& R, std::vector<cd>& T,
-              std::vector<int>& dep, bool allow_dep) {
+              std::vector<int>& dep, bool allow_dep, double dep_angle = kDepAngle) {
     R.assign((size_t)n * n, 0.0);
     T.assign((size_t)n * n, 0.0);
     dep.assign(n, 0);
@@ -526,7 +533,7 @@ bool chol_dep(const cd* G, const double* ref2, int n, std::vector<cd>& R, std::v
         double gkk = G[k * n + k].real();
         double d = gkk;
         for (int i = 0; i < k; ++i) d -= std::norm(R[i * n + k]);
-        bool dependent = !(gkk > 0.0) || !(d > kDepAngle * kDepAngle * gkk) ||
+        bool dependent = !(gkk > 0.0) || !(d > dep_angle * dep_angle * gkk) ||
                          (ref2 && !(d > kDepRoundoff * kDepRoundoff * ref2[k]));
         if (dependent) {
             if (!allow_dep) return false;
@@ -728,6 +735,11 @@ void gs_pass(helm_ctx* c, c128* Wp, int nb, int s, int sb, c128* H, bool repeat)
 // Unit roundoff of the Gram and update arithmetic (see kOrthTarget).
 double orth_unit(const helm_ctx* c) { return emulated(c) ? std::ldexp(1.0, -46) : std::ldexp(1.0, -53); }
 
+// Sine below which a block column counts as dependent (see kDepAngle).
+double dep_angle(const helm_ctx* c) {
+    return c->kfmt == helm::FMT_DD ? std::max(kDepAngle, 64.0 * std::sqrt(orth_unit(c))) : kDepAngle;
+}
+
 // kappa_F(R) = ||R||_F ||R^{-1}||_F over the independent columns: an upper
 // bound of the 2-norm condition number (at most n times it).
 double kappa_f(const std::vector<cd>& R, const std::vector<cd>& T, int n) {
@@ -763,7 +775,7 @@ bool needs_second_gs(const helm_ctx* c, int s, int sb, const std::vector<double>
         }
         std::vector<cd> R, T;
         std::vector<int> dep;
-        chol_dep(Gg.data(), r2.data(), n, R, T, dep, true);
+        chol_dep(Gg.data(), r2.data(), n, R, T, dep, true, dep_angle(c));
         for (int k = 0; k < n; ++k)
             if (dep[k] && r2[k] > 0.0) return true;
         const double kf = kappa_f(R, T, n);
@@ -824,7 +836,7 @@ helm_status block_qr(helm_ctx* c, c128* Win, int wfmt, c128* Vout, int nb, int s
         for (int k = 0; k < n; ++k) ref2[k] = extra2[g * sb + k] + Gg[k * n + k].real();
         std::vector<cd> T;
         std::vector<int> dep;
-        chol_dep(Gg.data(), ref2.data(), n, R1[g], T, dep, true);
+        chol_dep(Gg.data(), ref2.data(), n, R1[g], T, dep, true, dep_angle(c));
         for (int a = 0; a < sb; ++a)
             for (int b = 0; b < sb; ++b)
                 hT[(size_t)g * sb * sb + a * sb + b] = (a < n && b < n) ? T[a * n + b] : cd(0.0);
