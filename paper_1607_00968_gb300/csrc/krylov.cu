@@ -1112,8 +1112,15 @@ int gram_dd_parts(int s, int sb) {
 }
 
 constexpr int kMaxGramParts = 8;
+// Widest group the double-float Gram (and so the float-pair basis) serves.
+// Measured: groups of 32 strongly correlated right-hand sides (the 3D
+// workload, 256 sources 8 cells apart) let some groups stagnate when the
+// Gram and the basis carry 2^-46 instead of FP64's 2^-53; with the FP64 Gram
+// and a complex128 basis every group converges (45 cycles).  Narrow groups
+// (2, 4, 8 columns) behave like FP64.
+constexpr int kMaxDDGroup = 8;
 
-bool gram_dd_ok(int s, int sb) { return gram_dd_parts(s, sb) <= kMaxGramParts; }
+bool gram_dd_ok(int s, int sb) { return sb <= kMaxDDGroup && gram_dd_parts(s, sb) <= kMaxGramParts; }
 
 bool combine_dd_ok(int s, int sb) {
     return s <= kThreads && (size_t)((kThreads / s) * kCombineRows * s + ((s + sb - 1) / sb) * sb * sb) *
