@@ -71,6 +71,8 @@ def parse():
                     help="salt2d: the default line; the others are the small 2D, the 3D and the "
                          "uneven-batch configurations, measured with the same timing rules")
     ap.add_argument("--problems", type=int, default=200, help="batch workload: number of problems")
+    ap.add_argument("--only", default="", help="batch workload: comma-separated indices of the seeded "
+                                               "problem list to run (default: all)")
     return ap.parse_args()
 
 
@@ -439,7 +441,10 @@ def run_other(args):
             lv = inputs.default_levels(cells, 9000)
             specs.append(dict(k=k, cells=cells, f=round(f, 3), s=s, prec=prec, levels=lv,
                               cycle="K" if lv >= 4 else "V"))
-        chunk = 40          # contexts alive at once (their Krylov workspaces share HBM)
+        if args.only:
+            keep = {int(k) for k in args.only.split(",")}
+            specs = [d for d in specs if d["k"] in keep]
+        chunk = 20          # contexts alive at once (their Krylov workspaces share HBM)
 
         def run_chunk(sp):
             t0 = time.perf_counter()
@@ -461,7 +466,7 @@ def run_other(args):
                 S.close()
             del solvers, Qs, Us
             torch.cuda.empty_cache()    # give the cached blocks back: libhelm allocates with cudaMalloc
-            conv = [bool(np.all(i.relres <= TOL)) for i in infos]
+            conv = [bool(np.all(i.relres <= TOL)) and bool(np.all(i.status == 0)) for i in infos]
             cyc = [int(i.iters.max()) if i.iters.size else 0 for i in infos]
             return t1 - t0, t2 - t1, conv, cyc, int(st)
 

@@ -138,12 +138,14 @@ def _ptr(t) -> int:
 
 
 class Info:
-    """Per-column results of a solve (host numpy arrays)."""
+    """Per-column results of a solve (host numpy arrays).  They start as
+    iters -1, relres NaN, status -1, so a column the library never reached
+    (a call that failed before solving) cannot pass for converged."""
 
     def __init__(self, s):
-        self.iters = np.zeros(s, dtype=np.int32)
-        self.relres = np.zeros(s, dtype=np.float64)
-        self.status = np.zeros(s, dtype=np.int32)
+        self.iters = np.full(s, -1, dtype=np.int32)
+        self.relres = np.full(s, np.nan, dtype=np.float64)
+        self.status = np.full(s, -1, dtype=np.int32)
 
     def c_struct(self):
         return HelmInfo(self.iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
