@@ -6,15 +6,16 @@ its RMS rho, plus kappa = omega^2 m h^2, to a correction e ~ A^{-1} r in units
 of h^2 rho; FGMRES then uses z = V(v) + h^2 rho N(r/rho, kappa) (see
 include/helm.h, "Learned preconditioning stage").  Every forward, backward,
 loss and optimiser step runs in libhelm's kernels (helm_conv3x3,
-helm_conv3x3_wgrad, helm_conv3x3_flip, helm_learned_loss, helm_adam); this
-module holds the buffers and drives the loop.
+helm_conv3x3_wgrad, helm_conv3x3_flip, helm_learned_residual_loss,
+helm_adam), and so does the training data (helm_vcycle,
+helm_learned_residual_input, helm_learned_image_to_block); this module holds
+the buffers and drives the loop.
 
 Training data come from the solver itself on seeded random faulted/salt
-models.  Default loss: the residual left after the correction,
-||r - h^2 A (h^2 rho N)|| / ||r|| in the network's units (train_residual;
-the right-hand sides follow the stationary iteration's residual chain, and
-every pair costs one V-cycle, no solve).  Earlier loss: the error, target e
-= A^{-1} v - V(v) with A^{-1} v from a tight solve (make_pairs, train).
+models.  Loss: the residual left after the correction, ||r - h^2 A (h^2 rho
+N)|| / ||r|| in the network's units (train_residual; the right-hand sides
+follow the stationary iteration's residual chain, and every pair costs one
+V-cycle, no solve).
 
 Weights are saved as the flat blob of the ABI (bf16 weights + float biases)
 plus a JSON header (layer table, training record).
@@ -176,54 +177,6 @@ def _vp_stream(torch):
 # training data from the solver
 # ----------------------------------------------------------------------
 
-def make_pairs(seeds, freqs, cells=(512, 256), h=12.5, nsrc=32, steps=2, shift=0.2, levels=3,
-               tol=1e-7, chains=("residual", "arnoldi")):
-    """Returns (x bf16 [P, H, W, 16], t float [P, H, W, 2]) on the device.
-
-    Right-hand sides start at the normalised point sources and follow one or
-    both chains: "residual", v <- (v - A V(v)) normalised (the residuals of
-    the stationary iteration), and "arnoldi", v <- A V(v) orthogonalised
-    against v and normalised (one-vector Arnoldi, closer to the FGMRES
-    basis vectors)."""
-    import torch
-    lib = helm.load()
-    xs, ts = [], []
-    for seed in seeds:
-        for f in freqs:
-            P = inputs.random_problem_2d(seed, cells, h, f, nsrc, width=20, levels=levels)
-            S = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=shift, levels=levels, block=8,
-                            restart=10, prec="c64", max_restarts=200)
-            N = S.N
-            H, W = P.shape
-            b = torch.as_tensor(P.rhs()).cuda()                    # (s, N) ABI layout
-            for chain in chains:
-              v = (b / torch.linalg.vector_norm(b, dim=1, keepdim=True)).T.contiguous()  # (N, s)
-              for k in range(steps):
-                  z1 = S.vcycle(v, "c64")                            # (N, s) complex64
-                  x = torch.empty((nsrc, H, W, 16), dtype=torch.bfloat16, device="cuda")
-                  rho = torch.empty(nsrc, dtype=torch.float32, device="cuda")
-                  st = lib.helm_learned_input(S.ctx, _vp(v), _vp(z1), nsrc, _vp(x), _vp(rho))
-                  if st != 0:
-                      raise helm.HelmError(st, lib.helm_last_error(S.ctx).decode())
-                  u, info, _ = S.solve(v.T.contiguous(), tol)        # A^{-1} v, (s, N)
-                  e = (u.T - z1.to(torch.complex128)).to(torch.complex64).contiguous()
-                  t = torch.empty((nsrc, H, W, 2), dtype=torch.float32, device="cuda")
-                  st = lib.helm_learned_target(_vp(e), N, nsrc, _vp(rho), 1.0 / (h * h), _vp(t),
-                                               _vp_stream(torch))
-                  if st != 0:
-                      raise helm.HelmError(st, lib.helm_last_error(None).decode())
-                  xs.append(x)
-                  ts.append(t)
-                  Az = S.apply(z1.to(torch.complex128), 0, "A")
-                  if chain == "residual":
-                      r = v - Az
-                  else:
-                      r = Az - v * (v.conj() * Az).sum(dim=0, keepdim=True)
-                  v = (r / torch.linalg.vector_norm(r, dim=0, keepdim=True)).contiguous()
-            S.close()
-    return torch.cat(xs), torch.cat(ts)
-
-
 # ----------------------------------------------------------------------
 # residual-loss training: the residual of the corrected iterate
 # ----------------------------------------------------------------------
@@ -351,88 +304,24 @@ def train_residual(net: Network, configs, iters_per_config=64, batch=8, lr=1e-3,
     return hist
 
 
-def train(net: Network, x, t, iters=400, batch=8, lr=1e-3, seed=0, log_every=50):
-    """Adam on mini-batches of whole images; returns the loss history."""
-    import torch
-    lib = net.lib
-    P, H, W, _ = x.shape
-    g = np.random.Generator(np.random.PCG64(seed))
-    sums = torch.empty(2 * batch, dtype=torch.float32, device=x.device)
-    loss_d = torch.empty(1, dtype=torch.float32, device=x.device)
-    grad = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=x.device)
-    hist = []
-    t0 = time.perf_counter()
-    for it in range(iters):
-        idx = torch.as_tensor(g.choice(P, size=batch, replace=False), device=x.device)
-        xb, tb = x[idx].contiguous(), t[idx].contiguous()
-        out, acts = net.forward(xb, batch, H, W, keep=True)
-        st = lib.helm_learned_loss(_vp(out), _vp(tb), batch, H * W, _vp(sums), _vp(grad),
-                                   _vp(loss_d), _vp_stream(torch))
-        if st != 0:
-            raise helm.HelmError(st, lib.helm_last_error(None).decode())
-        net.zero_grad()
-        net.backward(acts, grad, batch, H, W)
-        net.adam(lr=lr)
-        if it % log_every == 0 or it == iters - 1:
-            hist.append((it, float(loss_d.item())))
-    net.record.update(dict(iters=iters, batch=batch, lr=lr, pairs=int(P),
-                           seconds=time.perf_counter() - t0, loss_history=hist))
-    return hist
-
-
-def evaluate_loss(net: Network, x, t, batch=8):
-    import torch
-    P, H, W, _ = x.shape
-    lib = net.lib
-    tot = 0.0
-    n = 0
-    sums = torch.empty(2 * batch, dtype=torch.float32, device=x.device)
-    loss_d = torch.empty(1, dtype=torch.float32, device=x.device)
-    grad = torch.empty((batch, H, W, 16), dtype=torch.bfloat16, device=x.device)
-    for i0 in range(0, P - batch + 1, batch):
-        out = net.forward(x[i0:i0 + batch].contiguous(), batch, H, W)
-        lib.helm_learned_loss(_vp(out), _vp(t[i0:i0 + batch].contiguous()), batch, H * W,
-                              _vp(sums), _vp(grad), _vp(loss_d), _vp_stream(torch))
-        tot += float(loss_d.item())
-        n += 1
-    return tot / max(n, 1)
-
-
 def main():
     """Train the stage on seeded models and save the blob:
-    python -m paper_1607_00968_gb300.learned OUT_PATH [ITERS_PER_CONFIG] [error]
-    (default: the residual loss, online over 40 model/frequency
-    configurations, about 20k pairs; `error` selects the earlier error
-    loss with ITERS total steps)."""
+    python -m paper_1607_00968_gb300.learned OUT_PATH [ITERS_PER_CONFIG]
+    (the residual loss, online over 40 model/frequency configurations,
+    about 20k pairs)."""
     import sys
     import torch
     out = sys.argv[1] if len(sys.argv) > 1 else "learned_salt2d.bin"
     torch.cuda.set_device(0)
-    if len(sys.argv) <= 3 or sys.argv[3] != "error":
-        ipc = int(sys.argv[2]) if len(sys.argv) > 2 else 64
-        configs = [(sd, f) for sd in range(101, 111) for f in (3.0, 4.5, 6.0, 7.5)]
-        net = Network(seed=0)
-        xv, rv, cv = residual_pairs(201, 5.0, nsrc=16, steps=8)
-        before = evaluate_residual_loss(net, xv, rv, cv)
-        train_residual(net, configs, iters_per_config=ipc)
-        after = evaluate_residual_loss(net, xv, rv, cv)
-        net.record.update(dict(val_loss_before=before, val_loss_after=after, val_seeds=[201],
-                               val_freq_hz=5.0, cells=[512, 256], h=12.5))
-        net.save(out)
-        print(json.dumps(net.record))
-        return
-    iters = int(sys.argv[2]) if len(sys.argv) > 2 else 600
-    t0 = time.perf_counter()
-    x, t = make_pairs(seeds=(101, 102, 103), freqs=(3.5, 5.0, 6.5), nsrc=32, steps=3)
-    xv, tv = make_pairs(seeds=(201,), freqs=(5.0,), nsrc=16, steps=3)
-    gen = time.perf_counter() - t0
+    ipc = int(sys.argv[2]) if len(sys.argv) > 2 else 64
+    configs = [(sd, f) for sd in range(101, 111) for f in (3.0, 4.5, 6.0, 7.5)]
     net = Network(seed=0)
-    before = evaluate_loss(net, xv, tv)
-    hist = train(net, x, t, iters=iters)
-    after = evaluate_loss(net, xv, tv)
-    net.record.update(dict(data_seconds=gen, val_loss_before=before, val_loss_after=after,
-                           train_seeds=[101, 102, 103], val_seeds=[201],
-                           train_freqs_hz=[3.5, 5.0, 6.5], cells=[512, 256], h=12.5))
+    xv, rv, cv = residual_pairs(201, 5.0, nsrc=16, steps=8)
+    before = evaluate_residual_loss(net, xv, rv, cv)
+    train_residual(net, configs, iters_per_config=ipc)
+    after = evaluate_residual_loss(net, xv, rv, cv)
+    net.record.update(dict(val_loss_before=before, val_loss_after=after, val_seeds=[201],
+                           val_freq_hz=5.0, cells=[512, 256], h=12.5))
     net.save(out)
     print(json.dumps(net.record))
 

@@ -146,31 +146,33 @@ def test_adam_step(lib):
     np.testing.assert_allclose(pb.float().cpu().numpy(), pp, rtol=1e-2, atol=1e-2)
 
 
-def test_training_lowers_loss_and_learned_solve_converges(lib):
-    """A short training run on small seeded problems lowers the validation
-    loss; the solve with the stage on reaches the tolerance (true FP64
-    residual of the oracle's operator) and its cycle count is reported beside
-    the plain cycle's."""
-    from paper_1607_00968_gb300 import helm, learned
-    cells, h = (128, 64), 25.0
-    x, t = learned.make_pairs(seeds=(11, 12), freqs=(5.0,), cells=cells, h=h, nsrc=8, steps=2)
-    xv, tv = learned.make_pairs(seeds=(21,), freqs=(5.0,), cells=cells, h=h, nsrc=8, steps=1)
-    net = learned.Network(seed=0)
-    before = learned.evaluate_loss(net, xv, tv, batch=4)
-    learned.train(net, x, t, iters=150, batch=4, lr=2e-3)
-    after = learned.evaluate_loss(net, xv, tv, batch=4)
-    assert after < before, (before, after)
-    P = I.random_problem_2d(31, cells, h, 5.0, 8, width=10, levels=3)
-    Q = torch.as_tensor(P.rhs()).cuda()
-    S0 = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=0.2, levels=3, block=4, restart=6, prec="c64")
-    S1 = helm.Solver(P.m, P.gamma, P.h, P.omega, shift=0.2, levels=3, block=4, restart=6,
-                     prec="learned", learned_weights=net.blob)
-    U0, i0, _ = S0.solve(Q, 1e-6)
-    U1, i1, _ = S1.solve(Q, 1e-6)
-    A = O.helmholtz_matrix(P.m, P.gamma, P.omega, P.h)
-    assert np.all(O.relres(A, U1.cpu().numpy().T, P.rhs().T) <= 1e-6)
-    print("\nlearned stage: val loss %.3f -> %.3f; cycles off %d, on %d"
-          % (before, after, i0.iters.max(), i1.iters.max()))
+def test_error_loss_kernel_matches_oracle(lib):
+    """helm_learned_target and helm_learned_loss (the error loss, kept in the
+    ABI beside the residual loss) against oracle/conv.loss and loss_grad."""
+    rng = np.random.default_rng(42)
+    B, H, W, s = 2, 7, 11, 2
+    N = H * W
+    e = (rng.standard_normal((N, s)) + 1j * rng.standard_normal((N, s))).astype(np.complex64)
+    rho = np.array([0.5, 2.0], dtype=np.float32)
+    t = torch.empty((s, N, 2), dtype=torch.float32, device="cuda")
+    e_d, rho_d = torch.as_tensor(e).cuda(), torch.as_tensor(rho).cuda()
+    assert lib.helm_learned_target(vp(e_d), N, s, vp(rho_d), 0.25, vp(t), stream()) == 0
+    tt = t.cpu().numpy().astype(np.float64)
+    for j in range(s):
+        np.testing.assert_allclose(tt[j, :, 0] + 1j * tt[j, :, 1], 0.25 * e[:, j] / rho[j], rtol=1e-6)
+    pred = rng.standard_normal((B, N, 16)).astype(np.float32)
+    sums = torch.empty(2 * B, dtype=torch.float32, device="cuda")
+    grad = torch.empty((B, N, 16), dtype=torch.bfloat16, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    p_d = torch.as_tensor(pred).cuda()
+    assert lib.helm_learned_loss(vp(p_d), vp(t), B, N, vp(sums), vp(grad), vp(loss), stream()) == 0
+    pr = pred[..., :2].astype(np.float64).reshape(B, H, W, 2)
+    tg = tt.reshape(B, H, W, 2)
+    ref = C.loss(pr, tg)
+    assert abs(float(loss.item()) - ref) <= 1e-5 * ref
+    g = grad.float().cpu().numpy()
+    assert rel(g[..., :2].reshape(B, H, W, 2), C.loss_grad(pr, tg)) < 1e-2
+    assert not np.any(g[..., 2:])
 
 
 # --------------------------------------------------------------------------
