@@ -50,14 +50,6 @@ void launch_kc_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, const double2
 template <typename T>
 void launch_axpy(const Launch& L, cplx<T>* y, const cplx<T>* x, long long n);
 
-// uout = one damped-Jacobi sweep of the fine operator on u + P ec (the
-// coarse-grid correction fused with the first post-smoothing sweep); uout
-// must not alias u; false (nothing launched) when the block shape has no
-// vectorised launch
-template <typename T, typename FT>
-bool launch_prolong_jacobi(const Launch& L, const FineOp<T>& op, const Grid& gc, const cplx<T>* ec,
-                           const cplx<T>* u, const cplx<FT>* f, cplx<T>* uout, int s, T w);
-
 // u += P ec
 template <typename T>
 void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const cplx<T>* ec,

@@ -375,83 +375,6 @@ __global__ void __launch_bounds__(256) k_prolong_add_v(Grid gf, Grid gc, const c
     stR<T, R>(u + e0, uv);
 }
 
-// u' = u + P ec at fine node (x, y, z), R columns from r0: the coarse nodes
-// around the fine node (one or two per axis, weight 1/2 per odd axis), summed
-// and added in the order k_prolong_add_v uses
-template <typename T, int R>
-__device__ __forceinline__ CV<T, R> prolonged(const Grid& gf, const Grid& gc, const cplx<T>* __restrict__ ec,
-                                             const cplx<T>* __restrict__ u, int x, int y, int z, int s,
-                                             int r0) {
-    const int nx = (x & 1) ? 2 : 1, ny = (y & 1) ? 2 : 1, nz = (gf.dim == 3 && (z & 1)) ? 2 : 1;
-    T wgt = T(1);
-    if (nx == 2) wgt *= T(0.5);
-    if (ny == 2) wgt *= T(0.5);
-    if (nz == 2) wgt *= T(0.5);
-    cplx<T> acc[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) acc[k] = mk<T>(0, 0);
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                if (c < nz && b < ny && a < nx) {
-                    CV<T, R> v = ldR<T, R>(ec + gc.index((x >> 1) + a, (y >> 1) + b, (z >> 1) + c) * s + r0);
-#pragma unroll
-                    for (int k = 0; k < R; ++k) acc[k] = acc[k] + v.v[k];
-                }
-            }
-    CV<T, R> uv = ldR<T, R>(u + gf.index(x, y, z) * s + r0);
-#pragma unroll
-    for (int k = 0; k < R; ++k) uv.v[k] = uv.v[k] + wgt * acc[k];
-    return uv;
-}
-
-// First post-smoothing sweep on the fine level fused with the coarse-grid
-// correction (Alg. "Two-grid cycle": correct, then relax): with u' = u + P ec
-// formed at the node and at its 2d stencil neighbours (the coarse correction
-// is small and read through the cache), uout = u' + w D^{-1} (f - M u').  The
-// arithmetic is that of k_prolong_add_v followed by k_jacobi_v, in the same
-// order, without writing u' and reading it back.
-template <typename T, typename FT, int R>
-__global__ void __launch_bounds__(256) k_prolong_jacobi_v(FineOp<T> op, Grid gc, const cplx<T>* __restrict__ ec,
-                                                           const cplx<T>* __restrict__ u,
-                                                           const cplx<FT>* __restrict__ f,
-                                                           cplx<T>* __restrict__ uout, int s, T w) {
-    VGEO_PROLOGUE(op.g)
-    const Grid& g = op.g;
-    const CV<T, R> uc = prolonged<T, R>(g, gc, ec, u, x, y, z, s, r0);
-    cplx<T> sum[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) sum[k] = mk<T>(0, 0);
-    auto add = [&](int xx, int yy, int zz) {
-        const CV<T, R> v = prolonged<T, R>(g, gc, ec, u, xx, yy, zz, s, r0);
-#pragma unroll
-        for (int k = 0; k < R; ++k) sum[k] = sum[k] + v.v[k];
-    };
-    if (x > 0) add(x - 1, y, z);
-    if (x < g.n1 - 1) add(x + 1, y, z);
-    if (y > 0) add(x, y - 1, z);
-    if (y < g.n2 - 1) add(x, y + 1, z);
-    if (g.dim == 3) {
-        if (z > 0) add(x, y, z - 1);
-        if (z < g.n3 - 1) add(x, y, z + 1);
-    }
-    const T dd = (T)(2 * g.dim);
-    const cplx<T> ci = ldg(op.c + node);
-    const cplx<T> d = op.diag_inv(node);
-    const CV<FT, R> fv = ldR<FT, R>(f + e0);
-    CV<T, R> outv;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const cplx<T> uk = uc.v[k];
-        const cplx<T> Au = op.inv_h2 * mk<T>(dd * uk.re - sum[k].re, dd * uk.im - sum[k].im) - ci * uk;
-        outv.v[k] = uk + w * (d * (cvt<T>(fv.v[k]) - Au));
-    }
-    stR<T, R>(uout + e0, outv);
-}
-
 // u = Minv f: tiled complex GEMM (n x n) * (n x s), 32 x 32 output tile per
 // block, 16-deep k tiles staged in shared memory, 4 outputs per thread.
 template <typename T>
@@ -892,21 +815,6 @@ void launch_prolong_add(const Launch& L, const Grid& gf, const Grid& gc, const c
     L.post();
 }
 
-template <typename T, typename FT>
-bool launch_prolong_jacobi(const Launch& L, const FineOp<T>& op, const Grid& gc, const cplx<T>* ec,
-                           const cplx<T>* u, const cplx<FT>* f, cplx<T>* uout, int s, T w) {
-    Geo G = geo_for(op.g, s);
-    if (!G.ok) return false;
-    const long long total = op.g.N * s;
-    L.pre(KID_JACOBI_FINE, total * (cb<FT>() + 2.0 * cb<T>()) + (double)gc.N * s * cb<T>() +
-                               op.g.N * (OpCost<FineOp<T>>::coef_bytes(op) + cb<T>()),
-          total * (OpCost<FineOp<T>>::flops(op) + 12.0 + 2.0 * (op.g.dim == 3 ? 8 : 4) * (2 * op.g.dim + 1)));
-    if (G.R == 2) k_prolong_jacobi_v<T, FT, 2><<<G.grid, G.block, 0, L.st>>>(op, gc, ec, u, f, uout, s, w);
-    else k_prolong_jacobi_v<T, FT, 1><<<G.grid, G.block, 0, L.st>>>(op, gc, ec, u, f, uout, s, w);
-    L.post();
-    return true;
-}
-
 template <typename T>
 void launch_dense_apply(const Launch& L, const cplx<T>* Minv, int n, const cplx<T>* f, cplx<T>* u,
                         int s) {
@@ -1006,9 +914,6 @@ void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count
                                                         const cplx<T>*, cplx<T>*, int);          \
     template void launch_prolong_add<T>(const Launch&, const Grid&, const Grid&, const cplx<T>*, \
                                         cplx<T>*, int);                                          \
-    template bool launch_prolong_jacobi<T, T>(const Launch&, const FineOp<T>&, const Grid&,       \
-                                              const cplx<T>*, const cplx<T>*, const cplx<T>*,     \
-                                              cplx<T>*, int, T);                                 \
     template void launch_axpy<T>(const Launch&, cplx<T>*, const cplx<T>*, long long);            \
     template void launch_coldot<T>(const Launch&, const cplx<T>*, const cplx<T>*, long long, int, \
                                    double2*, double2*, unsigned int*);                           \
@@ -1022,9 +927,6 @@ void launch_round_c64(const Launch& L, const c128* in, c64* out, long long count
 HELM_INST_T(float)
 HELM_INST_T(double)
 // complex64 cycle fed by a complex128 right-hand side (the Krylov basis)
-template bool launch_prolong_jacobi<float, double>(const Launch&, const FineOp<float>&, const Grid&,
-                                                   const cplx<float>*, const cplx<float>*,
-                                                   const cplx<double>*, cplx<float>*, int, float);
 template void launch_jacobi<float, double, FineOp<float>>(const Launch&, const FineOp<float>&,
                                                           const cplx<float>*, const cplx<double>*,
                                                           cplx<float>*, int, float);

@@ -389,29 +389,17 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
         helm::launch_axpy<T>(c->L(), ec, we, nxt.g.N * (long long)s);
     }
     cplx<T>* u = const_cast<cplx<T>*>(cur);
-    int k0 = 0;
-    if (l == 0 && u != nullptr && c->p.post > 0) {
-        // fine level: correction and first post-sweep in one pass
-        cplx<T>* dst = c->p.post == 1 ? out : (cur == bufA ? bufB : bufA);
-        if (helm::launch_prolong_jacobi<T, FT>(c->L(), fine_op<T>(c, true), nxt.g, ec, u, f, dst, s,
-                                               (T)c->p.jacobi_w)) {
-            cur = dst;
-            k0 = 1;
-        }
+    if (u == nullptr) {
+        u = bufA;
+        helm::launch_zero(c->L(), u, sizeof(cplx<T>) * lev.g.N * s);
     }
-    if (k0 == 0) {
-        if (u == nullptr) {
-            u = bufA;
-            helm::launch_zero(c->L(), u, sizeof(cplx<T>) * lev.g.N * s);
-        }
-        helm::launch_prolong_add<T>(c->L(), lev.g, nxt.g, ec, u, s);
-        cur = u;
-        if (c->p.post == 0) {
-            cudaMemcpyAsync(out, cur, sizeof(cplx<T>) * lev.g.N * s, cudaMemcpyDeviceToDevice, c->st);
-            return;
-        }
+    helm::launch_prolong_add<T>(c->L(), lev.g, nxt.g, ec, u, s);
+    cur = u;
+    if (c->p.post == 0) {
+        cudaMemcpyAsync(out, cur, sizeof(cplx<T>) * lev.g.N * s, cudaMemcpyDeviceToDevice, c->st);
+        return;
     }
-    for (int k = k0; k < c->p.post; ++k) {
+    for (int k = 0; k < c->p.post; ++k) {
         cplx<T>* dst = (k == c->p.post - 1) ? out : (cur == bufA ? bufB : bufA);
         smooth_level<T, FT>(c, l, cur, f, dst, s);
         cur = dst;

@@ -155,32 +155,6 @@ def test_coarsest_solve_and_vcycle(H, cells, levels):
     assert rel(z3, zr) < 1e-4
 
 
-@pytest.mark.parametrize("cells", [(40, 24), (16, 12, 8)])
-@pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_fused_correction_and_post_sweep_match_components(H, cells, prec):
-    """The cycle fuses the fine level's coarse-grid correction with its first
-    post-smoothing sweep (Alg. "Two-grid cycle": correct, then relax).  Two
-    levels: helm_vcycle against the same steps through the component entry
-    points, which run the correction and the sweep as separate kernels
-    (pre-sweeps from zero, residual restriction, coarsest solve,
-    prolongation and correction, post-sweeps): the same arithmetic, so the
-    results agree to rounding."""
-    m, g, h, om = layered(cells)
-    S = H.Solver(m, g, h, om, levels=2, coarse_tf32x3=True)
-    rng = np.random.default_rng(33)
-    s = 6
-    f = crand(rng, S.N, s)
-    dt = torch.complex128 if prec == "c128" else torch.complex64
-    z = S.vcycle(dev(f), prec).cpu().numpy()
-    fd = dev(f, dt)
-    u = S.smooth(fd, None, level=0, sweeps=2)
-    rc = S.restrict_residual(u, fd, level=0)
-    ec = S.coarse_solve(rc)
-    u = S.prolong_add(ec, u, level=0)
-    zc = S.smooth(fd, u, level=0, sweeps=2).cpu().numpy()
-    assert rel(z, zc) < (1e-13 if prec == "c128" else 1e-6)
-
-
 @pytest.mark.parametrize("s", [64, 100, 256])
 def test_coarsest_fp16_tcgen05_matches_mma_sync(H, s):
     """The FP16 coarsest product on tcgen05 (TMA tiles, tensor-memory
