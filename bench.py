@@ -419,7 +419,8 @@ def run_other(args):
         head = runs[-1][0]
         line.update({"metric": "Helmholtz RHS-solves/s to rel-res 1e-6 (%s)" % desc,
                      "value": round(res[head]["value"], 3), "ms_per_step": res[head]["ms_per_step"],
-                     "dtype": "c64+dd" if head == "c64" else "c128",
+                     # groups of more than 8 columns keep the FP64 Gram (double-float updates)
+                     "dtype": ("c64+dd" if kw["block"] <= 8 else "c64+f64/dd") if head == "c64" else "c128",
                      "config": dict(workload=desc, nodes=P.n_nodes, sources=Q.shape[0],
                                     omega=P.omega, **kw), "runs": res})
     else:
