@@ -287,28 +287,14 @@ void smooth_level(helm_ctx* c, int l, const cplx<T>* uin, const cplx<FT>* f, cpl
         helm::launch_jacobi<T, FT, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), uin, f, uout, s, w);
 }
 
-// rc = P^T (f - M_l u).  On the coarse levels, when the caller lends a
-// level-sized scratch block, the residual is formed once per node (9 or 27
-// complex products) and then restricted, instead of once per coarse node it
-// feeds (up to 2.25 / 3.4 times as many products).
 template <typename T, typename FT>
-void restrict_level(helm_ctx* c, int l, const cplx<T>* u, const cplx<FT>* f, cplx<T>* rc, int s,
-                    cplx<T>* scratch = nullptr) {
-    if (l == 0) {
+void restrict_level(helm_ctx* c, int l, const cplx<T>* u, const cplx<FT>* f, cplx<T>* rc, int s) {
+    if (l == 0)
         helm::launch_resid_restrict<T, FT, helm::FineOp<T>>(c->L(), fine_op<T>(c, true),
                                                             c->lv[1].g, u, f, rc, s);
-        return;
-    }
-    if constexpr (std::is_same<T, FT>::value) {
-        if (scratch && u) {
-            helm::launch_residual<T, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), u, f, scratch, s);
-            helm::launch_resid_restrict<T, T, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), c->lv[l + 1].g,
-                                                              nullptr, scratch, rc, s);
-            return;
-        }
-    }
-    helm::launch_resid_restrict<T, FT, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), c->lv[l + 1].g,
-                                                       u, f, rc, s);
+    else
+        helm::launch_resid_restrict<T, FT, helm::GalOp<T>>(c->L(), gal_op<T>(c, l), c->lv[l + 1].g,
+                                                           u, f, rc, s);
 }
 
 template <typename T>
@@ -388,9 +374,7 @@ void cycle(helm_ctx* c, int l, const cplx<FT>* f, cplx<T>* out, int s) {
     Level& nxt = c->lv[l + 1];
     cplx<T>* fc = reinterpret_cast<cplx<T>*>(nxt.f);
     cplx<T>* ec = reinterpret_cast<cplx<T>*>(nxt.e);
-    // the smoothing buffer that does not hold the iterate is free until the
-    // post-sweeps: it takes the coarse levels' residual
-    restrict_level<T, FT>(c, l, cur, f, fc, s, cur == bufA ? bufB : bufA);
+    restrict_level<T, FT>(c, l, cur, f, fc, s);
     if (c->p.cycle_gamma == 3 && l + 1 < Lv - 1)
         kcycle_correction<T>(c, l + 1, fc, ec, s);
     else
