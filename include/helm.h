@@ -174,7 +174,9 @@ helm_status helm_setup(const double* m, const double* gamma_tilde,
 /* Solve A U = Q for s right-hand sides to per-column relative residual tol
    (FP64, true residual), X_0 = 0 (Sec. 5.3: block FGMRES preconditioned by
    the shifted-Laplacian cycle).  Q, U: device complex128, ABI layout, N x s.
-   A zero column gives a zero solution with relres 0.  info may be NULL. */
+   A zero column gives a zero solution with relres 0.  info may be NULL.
+   s = 0 returns HELM_OK and touches nothing (Q and U may then be NULL);
+   s < 0, tol <= 0, or a NULL Q or U with s > 0 gives HELM_ERR_ARG. */
 helm_status helm_solve(helm_ctx* ctx, const void* Q, int s, double tol,
                        void* U, helm_info* info);
 
@@ -186,7 +188,10 @@ helm_status helm_adjoint(helm_ctx* ctx, const void* B, int s, double tol,
 
 /* helm_solve with HOST complex128 buffers (ABI layout): copies Q to the
    device, solves, copies U back, all on the context's stream.  Pinned host
-   memory makes the copies asynchronous DMA; pageable memory works too. */
+   memory makes the copies asynchronous DMA; pageable memory works too.  The
+   device staging of Q and U is owned by the context and holds as many
+   columns as its workspace; s = 0 and bad arguments behave as in
+   helm_solve. */
 helm_status helm_solve_host(helm_ctx* ctx, const void* Q_host, int s,
                             double tol, void* U_host, helm_info* info);
 

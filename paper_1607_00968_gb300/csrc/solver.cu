@@ -1651,14 +1651,18 @@ helm_status helm_adjoint(helm_ctx* ctx, const void* B, int s, double tol, void* 
 helm_status helm_solve_host(helm_ctx* c, const void* Q_host, int s, double tol, void* U_host,
                             helm_info* info) {
     if (!c) return fail(nullptr, HELM_ERR_ARG, "null context");
-    if (s <= 0 || !Q_host || !U_host) return fail(c, HELM_ERR_ARG, "bad arguments to solve_host");
+    if (s < 0 || (s > 0 && (!Q_host || !U_host)) || !(tol > 0.0))
+        return fail(c, HELM_ERR_ARG, "bad arguments to solve_host");
+    if (s == 0) return HELM_OK;
     helm_status st = ensure_workspace(c, s);
     if (st != HELM_OK) return st;
+    // The device staging holds s_cap columns, so every later call of at most
+    // s_cap columns fits; a call that raises s_cap frees it (free_workspace)
+    // and it is allocated again at the new capacity.
+    const size_t cap_bytes = sizeof(c128) * (size_t)c->N() * c->s_cap;
     const size_t bytes = sizeof(c128) * (size_t)c->N() * s;
-    if (!c->abi_in) {
-        CUDA_TRY(c, dalloc(&c->abi_in, bytes));
-        CUDA_TRY(c, dalloc(&c->abi_out, bytes));
-    }
+    if (!c->abi_in) CUDA_TRY(c, dalloc(&c->abi_in, cap_bytes));
+    if (!c->abi_out) CUDA_TRY(c, dalloc(&c->abi_out, cap_bytes));
     CUDA_TRY(c, cudaMemcpyAsync(c->abi_in, Q_host, bytes, cudaMemcpyHostToDevice, c->st));
     helm_status r = solve_internal(c, c->abi_in, s, tol, c->abi_out, info, false);
     if (r == HELM_ERR_ARG || r == HELM_ERR_CUDA || r == HELM_ERR_NOMEM) return r;

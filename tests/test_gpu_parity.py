@@ -330,6 +330,31 @@ def test_not_converged_returns_best_iterate(H):
     assert np.all(rr < 1.0)
 
 
+def test_solve_host_buffers_match_device_solve(H):
+    """helm_solve_host (pinned host buffers, device staging owned by the
+    context) gives the device solve's result.  The calls grow from 2 to 8
+    columns within a workspace set up for 8, so each reuses the staging
+    allocated by the first.  Empty blocks return OK and touch nothing."""
+    m, g, h, om = layered((64, 32), width=6)
+    S = H.Solver(m, g, h, om, levels=3, block=4, prec="c64")
+    Q = I.point_sources(m.shape, I.line_positions(m.shape, 8, 2, 6), h)
+    S.solve(dev(Q), tol=1e-8)                     # workspace for 8 columns
+    A = O.helmholtz_matrix(m, g, om, h)
+    for s in (2, 5, 8):
+        Ud, _, _ = S.solve(dev(Q[:s]), tol=1e-8)
+        Qh = torch.as_tensor(np.ascontiguousarray(Q[:s])).pin_memory()
+        Uh = torch.zeros_like(Qh).pin_memory()
+        info, st = S.solve_host(Qh, Uh, tol=1e-8)
+        assert st == 0 and np.all(info.status == 0)
+        assert rel(Uh.numpy(), Ud.cpu().numpy()) <= 1e-12
+        assert np.all(O.relres(A, Uh.numpy().T, Q[:s].T) <= 1e-8)
+    U0, info0, st0 = S.solve(dev(np.zeros((0, S.N), dtype=complex)), tol=1e-6)
+    assert st0 == 0 and tuple(U0.shape) == (0, S.N)
+    e = torch.zeros((0, S.N), dtype=torch.complex128)
+    _, st0h = S.solve_host(e, e.clone(), tol=1e-6)
+    assert st0h == 0
+
+
 @pytest.mark.parametrize("prec,cycle", [("c128", "V"), ("c64", "V"), ("c64", "K")])
 def test_graph_replay_matches_direct_launches(H, prec, cycle):
     """The FGMRES step replayed from CUDA graphs gives the directly launched
