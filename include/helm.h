@@ -386,7 +386,10 @@ helm_status helm_learned_loss(const float* pred, const float* t, int batch, long
  * (half re, half im; fields_half = 1), the storage Sec. 2.4 uses for the
  * forward fields.  Data blocks (W, d_obs, jv output): device complex128,
  * s x nrec (column j = source j).  Solves use the context's solver and tol;
- * each call allocates its temporaries.
+ * each call allocates its temporaries (HELM_ERR_NOMEM if it cannot; nothing
+ * is kept).  Receiver indices must lie in [0, N): each call copies the nrec
+ * indices to the host and returns HELM_ERR_ARG, before any kernel runs, if
+ * one does not.
  * ------------------------------------------------------------------- */
 /* U16[e] = (half) U[e] for N*s complex values. */
 helm_status helm_fields_to_half(const void* U, long long N, int s, void* U16, void* stream);

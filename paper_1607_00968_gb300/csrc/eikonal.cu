@@ -677,6 +677,7 @@ helm_status helm_eik_create(int dim, const int* n, double h, int ns_max, void* s
     if (c == cudaSuccess) c = cudaMalloc(&e->status, sizeof(int) * ns_max);
     if (c == cudaSuccess) c = cudaMalloc(&e->dmap, sizeof(int) * ns_max);
     if (c != cudaSuccess) {
+        (void)cudaGetLastError();   // reported here; not again by a later error check
         helm_eik_destroy(e);
         return eik_fail(nullptr, c == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA,
                         std::string("cudaMalloc: ") + cudaGetErrorString(c));

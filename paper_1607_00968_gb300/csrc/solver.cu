@@ -237,9 +237,27 @@ helm_status fail(helm_ctx* c, helm_status s, const std::string& msg) {
                         std::string(#expr) + ": " + cudaGetErrorString(e_));           \
     } while (0)
 
+// A failed allocation is reported through the return value only: the
+// runtime's pending error is cleared, so that the next cudaGetLastError (the
+// check at the end of a later call) does not report it a second time.
 template <typename P>
 cudaError_t dalloc(P** p, size_t bytes) {
-    return cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+    }
+    return e;
+}
+
+template <typename P>
+cudaError_t halloc_pinned(P** p, size_t bytes) {
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+    }
+    return e;
 }
 
 void dfree(void* p) {
@@ -493,7 +511,7 @@ helm_status ensure_workspace(helm_ctx* c, int s) {
     long long blk = (long long)G * sb * sb;
     c->small_elems = std::max(2 * (m + 1) * blk + 2 * blk + (long long)m * blk, 10 * blk) + 4LL * s + 64;
     CUDA_TRY(c, dalloc(&c->small, sizeof(c128) * c->small_elems));
-    CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->hsmall), sizeof(c128) * c->small_elems));
+    CUDA_TRY(c, halloc_pinned(&c->hsmall, sizeof(c128) * c->small_elems));
     CUDA_TRY(c, dalloc(&c->dmask, sizeof(int) * s));
     CUDA_TRY(c, dalloc(&c->csplit, sizeof(float4) * (size_t)(m + 1) * blk));
     CUDA_TRY(c, dalloc(&c->dense_scratch, sizeof(float) * helm::dense_tc_scratch_floats(c->nc, s)));
@@ -1469,6 +1487,34 @@ helm_status smooth_t(helm_ctx* c, int level, const void* u_in, const void* f, vo
     return sync(c);
 }
 
+// Receiver indices (device int array) must name nodes of the fine grid: they
+// are copied to the host and checked before any kernel reads through them.
+helm_status check_receivers(helm_ctx* c, const int* recv, int nrec) {
+    std::vector<int> h((size_t)nrec);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), recv, sizeof(int) * (size_t)nrec, cudaMemcpyDefault, c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+    const long long N = c->N();
+    for (int r = 0; r < nrec; ++r)
+        if (h[r] < 0 || h[r] >= N)
+            return fail(c, HELM_ERR_ARG, "receiver index " + std::to_string(h[r]) + " outside [0, N)");
+    return HELM_OK;
+}
+
+// Two device temporaries of a call; on failure neither is kept.
+helm_status alloc_pair(helm_ctx* c, void** a, size_t abytes, void** b, size_t bbytes) {
+    *a = *b = nullptr;
+    cudaError_t e = dalloc(a, abytes);
+    if (e == cudaSuccess) e = dalloc(b, bbytes);
+    if (e != cudaSuccess) {
+        dfree(*a);
+        dfree(*b);
+        *a = *b = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? HELM_ERR_NOMEM : HELM_ERR_CUDA,
+                    std::string("device temporaries: ") + cudaGetErrorString(e));
+    }
+    return HELM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -2112,10 +2158,13 @@ helm_status helm_fwi_jv(helm_ctx* c, const void* fields, int fields_half, int s,
                         const int* recv, int nrec, double tol, void* out) {
     if (!c || !fields || !v || !recv || !out || s < 1 || nrec < 1)
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_jv");
+    helm_status sr = check_receivers(c, recv, nrec);
+    if (sr != HELM_OK) return sr;
     const long long N = c->N();
     c128 *rhs = nullptr, *w = nullptr;
-    CUDA_TRY(c, dalloc(&rhs, sizeof(c128) * (size_t)N * s));
-    CUDA_TRY(c, dalloc(&w, sizeof(c128) * (size_t)N * s));
+    sr = alloc_pair(c, reinterpret_cast<void**>(&rhs), sizeof(c128) * (size_t)N * s, reinterpret_cast<void**>(&w),
+                    sizeof(c128) * (size_t)N * s);
+    if (sr != HELM_OK) return sr;
     helm::launch_jv_rhs(c->L(), fields, fields_half, N, s, c->dadm, v, rhs);
     helm_status st = helm_solve(c, rhs, s, tol, w, nullptr);
     if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
@@ -2132,10 +2181,13 @@ helm_status helm_fwi_jtw(helm_ctx* c, const void* fields, int fields_half, int s
                          const int* recv, int nrec, double tol, double* out) {
     if (!c || !fields || !W || !recv || !out || s < 1 || nrec < 1)
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_jtw");
+    helm_status sr = check_receivers(c, recv, nrec);
+    if (sr != HELM_OK) return sr;
     const long long N = c->N();
     c128 *pw = nullptr, *lam = nullptr;
-    CUDA_TRY(c, dalloc(&pw, sizeof(c128) * (size_t)N * s));
-    CUDA_TRY(c, dalloc(&lam, sizeof(c128) * (size_t)N * s));
+    sr = alloc_pair(c, reinterpret_cast<void**>(&pw), sizeof(c128) * (size_t)N * s, reinterpret_cast<void**>(&lam),
+                    sizeof(c128) * (size_t)N * s);
+    if (sr != HELM_OK) return sr;
     helm::launch_scatter(c->L(), static_cast<const c128*>(W), N, s, recv, nrec, pw);
     helm_status st = helm_adjoint(c, pw, s, tol, lam, nullptr);
     if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
@@ -2153,11 +2205,14 @@ helm_status helm_fwi_gradient(helm_ctx* c, const void* Q, int s, const void* d_o
                               void* U_out) {
     if (!c || !Q || !d_obs || !recv || !grad || s < 1 || nrec < 1)
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_fwi_gradient");
+    helm_status sr = check_receivers(c, recv, nrec);
+    if (sr != HELM_OK) return sr;
     const long long N = c->N();
     c128 *U = nullptr, *D = nullptr;
     void* U16 = nullptr;
-    CUDA_TRY(c, dalloc(&U, sizeof(c128) * (size_t)N * s));
-    CUDA_TRY(c, dalloc(&D, sizeof(c128) * (size_t)nrec * s));
+    sr = alloc_pair(c, reinterpret_cast<void**>(&U), sizeof(c128) * (size_t)N * s, reinterpret_cast<void**>(&D),
+                    sizeof(c128) * (size_t)nrec * s);
+    if (sr != HELM_OK) return sr;
     helm_status st = helm_solve(c, Q, s, tol, U, nullptr);
     if (st == HELM_OK || st == HELM_NOT_CONVERGED) {
         helm::launch_gather(c->L(), U, N, s, recv, nrec, static_cast<const c128*>(d_obs), D);
