@@ -219,7 +219,10 @@ const char* helm_last_error(const helm_ctx* ctx);
  * the hot-path steps one by one so that each can be checked on its own.
  * `prec`: 0 = complex128 vectors and FP64 arithmetic, 1 = complex64 vectors
  * and FP32 arithmetic (coefficients rounded from the FP64 set-up).
- * Level 0 is the fine grid; level levels-1 the coarsest.
+ * Level 0 is the fine grid; level levels-1 the coarsest.  An output must
+ * not share memory with an input of the same call (the stencil kernels read
+ * the neighbours of the nodes they write); helm_prolong_add, which updates u
+ * in place, is the exception.
  * ------------------------------------------------------------------- */
 
 /* Nodes per axis (nodes[3], unused axes 1) and node count of a level. */

@@ -691,6 +691,7 @@ helm_status helm_eik_forward(helm_eik* e, const double* m, const int* src, int n
     if (!e) return eik_fail(nullptr, HELM_ERR_ARG, "null workspace");
     if (!m || !src || ns < 1 || ns > e->ns_max) return eik_fail(e, HELM_ERR_ARG, "bad m, src or ns");
     const EikGrid& g = e->g;
+    e->ns = 0;   // the products need a completed marching of these sources
     e->hsrc.assign(3 * (size_t)ns, 0);
     for (int b = 0; b < ns; ++b)
         for (int a = 0; a < g.d; ++a) {

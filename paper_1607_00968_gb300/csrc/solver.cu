@@ -2088,8 +2088,9 @@ helm_status helm_learned_input(helm_ctx* c, const void* f, const void* z, int s,
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_learned_input");
     c64* r = nullptr;
     float* rho2 = nullptr;
-    CUDA_TRY(c, dalloc(&r, sizeof(c64) * (size_t)c->N() * s));
-    CUDA_TRY(c, dalloc(&rho2, sizeof(float) * s));
+    helm_status sa = alloc_pair(c, reinterpret_cast<void**>(&r), sizeof(c64) * (size_t)c->N() * s,
+                                reinterpret_cast<void**>(&rho2), sizeof(float) * s);
+    if (sa != HELM_OK) return sa;
     helm::launch_learned_residual(c->L(), fine_op<float>(c, false), static_cast<const c128*>(f),
                                   static_cast<const c64*>(z), r, s, rho2, rho_out);
     helm::launch_pack_input(c->L(), r, (int)c->N(), s, rho_out, c->kappa, x_out);
@@ -2105,8 +2106,9 @@ helm_status helm_learned_residual_input(helm_ctx* c, const void* f, const void* 
         return fail(c, HELM_ERR_ARG, "bad arguments to helm_learned_residual_input");
     c64* r = nullptr;
     float* rho2 = nullptr;
-    CUDA_TRY(c, dalloc(&r, sizeof(c64) * (size_t)c->N() * s));
-    CUDA_TRY(c, dalloc(&rho2, sizeof(float) * s));
+    helm_status sa = alloc_pair(c, reinterpret_cast<void**>(&r), sizeof(c64) * (size_t)c->N() * s,
+                                reinterpret_cast<void**>(&rho2), sizeof(float) * s);
+    if (sa != HELM_OK) return sa;
     helm::launch_learned_residual(c->L(), fine_op<float>(c, false), static_cast<const c128*>(f),
                                   static_cast<const c64*>(z), r, s, rho2, rho_out);
     helm::launch_pack_input(c->L(), r, (int)c->N(), s, rho_out, c->kappa, x_out);
