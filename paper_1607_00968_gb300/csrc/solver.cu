@@ -192,6 +192,8 @@ struct helm_ctx {
     int* dmask = nullptr;
     float4* csplit = nullptr; // split (float pair) coefficients of the dd block updates
     c128* hsmall = nullptr;  // pinned host mirror of `small`
+    // counter of the generator that draws replacement directions for
+    // dependent columns (rank rule); every solve starts it at the same value
     unsigned long long rng_counter = 0x5eed;
     helm::Profiler* prof = nullptr;
     // CUDA graphs of the FGMRES step (one per (s, j)), captured on a private
@@ -1451,6 +1453,9 @@ helm_status solve_internal(helm_ctx* c, const c128* Qd, int s, double tol, c128*
     if (s == 0) return HELM_OK;
     helm_status st = ensure_workspace(c, s);
     if (st != HELM_OK) return st;
+    // the same block gives the same result on every call: the draws for
+    // dependent columns do not depend on what the context solved before
+    c->rng_counter = 0x5eed;
     const long long N = c->N();
     helm::launch_to_internal(c->L(), Qd, c->Bint, N, s, conjugate);
     if (c->p.krylov == 1)
