@@ -28,6 +28,34 @@ def test_double_float_peak_formula():
     assert abs(bench.dd_peak_tflops(76, 2070.0) - bench.dd_peak_tflops(152, 2070.0) / 2) < 1e-12
 
 
+def test_headline_convergence_rule():
+    """The bench counts a solve only when every column ended at true relres
+    <= tol with status OK; one column above tol, one non-OK status, or one
+    column the library never reached withholds it."""
+    import bench
+    from paper_1607_00968_gb300 import helm
+    tol = 1e-6
+    ok = helm.Info(4)
+    ok.iters[:] = 10
+    ok.relres[:] = [1e-7, 5e-7, 1e-6, 0.0]       # tol itself and a zero column count
+    ok.status[:] = 0
+    assert bench.converged(ok, tol)
+    above = helm.Info(4)
+    above.relres[:] = [1e-7, 1.0000001e-6, 1e-7, 1e-7]
+    above.status[:] = 0
+    assert not bench.converged(above, tol)
+    flagged = helm.Info(2)
+    flagged.relres[:] = 1e-8
+    flagged.status[:] = [0, 1]                   # HELM_NOT_CONVERGED on one column
+    assert not bench.converged(flagged, tol)
+    unreached = helm.Info(3)                     # NaN / -1 sentinels
+    assert not bench.converged(unreached, tol)
+    partial = helm.Info(3)
+    partial.relres[:2] = 1e-8
+    partial.status[:2] = 0                       # the third column never written
+    assert not bench.converged(partial, tol)
+
+
 def test_info_starts_unconverged():
     """A column the library never reached cannot pass for converged: the
     binding's result arrays start as iters -1, relres NaN, status -1."""
